@@ -1,0 +1,171 @@
+/*
+ * ibf.h -- C ABI of the GB300 pressure-projection library (libibf.so).
+ *
+ * The library computes the projection step of the fractional-step
+ * Navier-Stokes solver of IB-Flows (Section "Fluid Mechanics"):
+ *
+ *   Eq. (elliptic):  lap(phi) = div(u*) / (alpha dt)          (q = 0)
+ *   Eq. (velsolen):  u_{n+1}  = u* - alpha dt grad(phi)
+ *
+ * on the staggered Cartesian grid with second-order centred differences, x and
+ * y periodic with uniform spacing, z bounded by walls with an arbitrary
+ * (stretched) spacing and a homogeneous Neumann condition for phi, the
+ * arbitrary constant of phi fixed by a reference value (same section).  The
+ * Poisson equation is solved directly as the paper's solver does (Section
+ * "Fluid domain", projection paragraph): real FFTs in x and y leave one
+ * tridiagonal system along z per horizontal mode.  Everything runs on one GPU
+ * in hand-written sm_103a kernels; there is no CPU fallback.
+ *
+ * Discretisation fixed by this library (the paper states only "staggered,
+ * second-order centred"):
+ *   cells i < nx, j < ny, k < nz;  dx = lx/nx, dy = ly/ny;
+ *   z faces zf[0..nz] with zf[0] = 0, zf[nz] = lz;  hz_k = zf[k+1]-zf[k];
+ *   cell centres zc_k = (zf_k + zf_{k+1})/2;  gz_k = zc_k - zc_{k-1};
+ *   u[k][j][i] on the x-face x = i dx (left face of cell i), shape [nz][ny][nx];
+ *   v[k][j][i] on the y-face y = j dy, shape [nz][ny][nx];
+ *   w[k][j][i] on the z-face z = zf[k], shape [nz+1][ny][nx] (k = 0, nz: walls);
+ *   p (phi)   at cell centres, shape [nz][ny][nx];  all float64, i fastest.
+ *   (D u)_c = (u_{i+1}-u_i)/dx + (v_{j+1}-v_j)/dy + (w_{k+1}-w_k)/hz_k (periodic wrap);
+ *   G phi on interior faces (difference over dx, dy or gz_k), zero on the walls,
+ *   so the wall-normal velocity is left unchanged.
+ *   Reference value: the volume-weighted mean of the right-hand side is removed
+ *   (its value is reported as the compatibility defect) and phi is returned
+ *   with zero volume-weighted mean (weights dx dy hz_k).
+ *
+ * Threading: a plan may be used by one host thread and one stream at a time.
+ * Calls never throw; every entry point returns an ibf_status.
+ */
+#ifndef IBF_H
+#define IBF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IBF_VERSION_MAJOR 0
+#define IBF_VERSION_MINOR 1
+#define IBF_MAX_GRIDS 4096
+
+typedef enum ibf_status {
+    IBF_OK = 0,
+    IBF_ERR_INVALID_ARG = 1,      /* null pointer, non-positive size, bad enum, ... */
+    IBF_ERR_UNSUPPORTED_SIZE = 2, /* nx or ny not a product of two factors in {1,2,3,4,6,8,12,16,24,32} */
+    IBF_ERR_OOM = 3,              /* a device allocation in ibf_projection_plan failed */
+    IBF_ERR_CUDA = 4,             /* a CUDA runtime call failed (message: ibf_last_error) */
+    IBF_ERR_TIMEOUT = 5,          /* a bounded device wait gave up (reported by ibf_plan_sync_status) */
+    IBF_ERR_NONFINITE = 6,        /* NaN or Inf met in the right-hand side (ibf_plan_sync_status) */
+    IBF_WARN_INCOMPATIBLE_RHS = 7,/* |compatibility defect| above 1e-8 of the RHS scale; result still returned */
+    IBF_ERR_UNSUPPORTED_BC = 8    /* a boundary condition this build does not implement */
+} ibf_status;
+
+typedef enum ibf_bc {
+    IBF_BC_PERIODIC = 0,
+    IBF_BC_NEUMANN = 1,           /* wall: prescribed normal velocity, homogeneous Neumann phi */
+    IBF_BC_DIRICHLET = 2          /* homogeneous Dirichlet phi (not implemented: UNSUPPORTED_BC) */
+} ibf_bc;
+
+typedef enum ibf_precision {
+    IBF_FP64 = 0,  /* fp64 transforms, tridiagonal sweeps and stencils */
+    IBF_MIXED = 1  /* fp32 transforms and sweeps; float-float (2 x fp32) stencils, residual and
+                      accumulation; refine_steps iterative-refinement sweeps */
+} ibf_precision;
+
+/* One grid of the batch.  Copied by ibf_projection_plan; the caller keeps ownership of zf. */
+typedef struct ibf_grid {
+    int nx, ny, nz;         /* cells; nx, ny as for IBF_ERR_UNSUPPORTED_SIZE, nz >= 1 */
+    double lx, ly, lz;      /* box lengths (> 0) */
+    const double *zf;       /* HOST pointer to nz+1 strictly ascending z faces with zf[0] = 0 and
+                               zf[nz] = lz, or NULL to use the tanh map below */
+    double beta;            /* tanh clustering factor when zf == NULL:
+                               zf_k = lz/2 (1 + tanh(beta (2k/nz - 1)) / tanh(beta)); beta = 0: uniform */
+    int bc_x, bc_y;         /* ibf_bc; this build: IBF_BC_PERIODIC */
+    int bc_zlo, bc_zhi;     /* ibf_bc; this build: IBF_BC_NEUMANN */
+} ibf_grid;
+
+typedef struct ibf_opts {
+    int precision;          /* ibf_precision */
+    int refine_steps;       /* IBF_MIXED only: iterative-refinement sweeps after the first solve (0..8) */
+    int autotune;           /* 1: time candidate launch shapes at plan time (uses scratch, synchronises) */
+    int reserved;           /* must be 0 */
+} ibf_opts;
+
+/* DEVICE pointers (float64, layouts above) of one grid. */
+typedef struct ibf_fields {
+    double *u, *v, *w, *p;
+} ibf_fields;
+
+/* Optional DEVICE outputs, each an array of ngrids doubles (any pointer may be NULL).
+ * max_div     : max_c |(D u_{n+1})_c| of the returned velocity;
+ * max_div_in  : max_c |(D u*)_c|;
+ * compat      : removed volume-weighted mean of div(u*)/(alpha dt). */
+typedef struct ibf_stats {
+    double *max_div, *max_div_in, *compat;
+} ibf_stats;
+
+typedef struct ibf_plan ibf_plan;
+
+/* Build a plan for ngrids grids (1 <= ngrids <= IBF_MAX_GRIDS) on CUDA device `device`.
+ * Validates every descriptor on the host, builds the z coefficients, the modified
+ * wavenumbers, twiddle tables and the per-mode pivot tables of the tridiagonal
+ * solves (float64 arithmetic), picks launch shapes (timed if opts->autotune),
+ * and allocates all device workspace.  Synchronises the device.
+ * On success *plan owns the workspace; on error *plan is NULL and nothing leaks.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, UNSUPPORTED_BC, OOM, CUDA. */
+ibf_status ibf_projection_plan(ibf_plan **plan, const ibf_grid *grids, int ngrids,
+                               const ibf_opts *opts, int device);
+
+/* Project grid g's u* = in[g] into out[g] (arrays of ngrids ibf_fields):
+ * out.p <- phi, out.u/v/w <- u* - alpha dt G phi.  in[g].p is ignored.  out may
+ * alias in (in place).  dt > 0, alpha > 0.  stats may be NULL.  stream is a
+ * cudaStream_t (NULL: legacy default stream).  Enqueues kernels only: no
+ * allocation, no host synchronisation, so it can be captured into a CUDA graph.
+ * Device-side errors are recorded in the plan and returned by
+ * ibf_plan_sync_status.  Errors: INVALID_ARG, CUDA. */
+ibf_status ibf_project(ibf_plan *plan, const ibf_fields *in, const ibf_fields *out,
+                       double dt, double alpha, const ibf_stats *stats, void *stream);
+
+/* Adjoint (vector-Jacobian product) of the map u* -> (u, phi) of ibf_project for the
+ * Euclidean inner product:  grad_in = g_u + D^T S^-T (g_phi/(alpha dt) - G^T g_u),
+ * S^-T = V S^-1 V^-1 with V = diag(dx dy hz_k), computed with the same solver.
+ * grad_out[g].{u,v,w} = g_u (device, same shapes as the velocity), grad_out[g].p = g_phi
+ * (may be NULL = zero).  grad_in[g].{u,v,w} receive the gradient with respect to u*
+ * (grad_in[g].p ignored).  grad_in may alias grad_out's velocity arrays.  Same
+ * stream/capture rules as ibf_project. */
+ibf_status ibf_project_backward(ibf_plan *plan, const ibf_fields *grad_out, const ibf_fields *grad_in,
+                                double dt, double alpha, void *stream);
+
+/* Synchronise the plan's last stream, return and clear the device error word
+ * (IBF_OK, IBF_ERR_TIMEOUT, IBF_ERR_NONFINITE or IBF_WARN_INCOMPATIBLE_RHS). */
+ibf_status ibf_plan_sync_status(ibf_plan *plan);
+
+/* Release all workspace (synchronises the plan's device).  NULL is accepted. */
+ibf_status ibf_plan_destroy(ibf_plan *plan);
+
+/* Static description of a status code. */
+const char *ibf_status_string(ibf_status s);
+
+/* Text of the last CUDA error seen by this thread's calls (empty if none). */
+const char *ibf_last_error(void);
+
+/* Plan facts: workspace bytes, and per-grid launch choices. */
+typedef struct ibf_plan_info {
+    long long workspace_bytes;
+    int ngrids;
+    int precision;
+    int refine_steps;
+    long long total_cells;
+} ibf_plan_info;
+ibf_status ibf_plan_get_info(const ibf_plan *plan, ibf_plan_info *info);
+
+/* Per-kernel timing with CUDA events recorded on the call's stream around every
+ * launch (off by default).  ibf_profile_read fills up to `cap` entries: kernel
+ * name (static string), launch count and summed milliseconds since the last
+ * reset; it synchronises the plan's last stream.  Returns the number of entries. */
+ibf_status ibf_profile_enable(ibf_plan *plan, int enable);
+int ibf_profile_read(ibf_plan *plan, const char **names, long long *launches, double *ms, int cap);
+ibf_status ibf_profile_reset(ibf_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBF_H */

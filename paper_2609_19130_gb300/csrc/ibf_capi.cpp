@@ -1,0 +1,651 @@
+// ibf_capi.cpp -- host side of libibf: plan construction (validation, grid
+// geometry, tridiagonal coefficients, twiddles, pivot tables, launch shapes,
+// workspace) and the C ABI declared in include/ibf.h.
+#include "../../include/ibf.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ibf_internal.h"
+
+using namespace ibf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ibf_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return IBF_ERR_CUDA;
+}
+
+const int kFftSizes[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
+
+bool in_sizes(int n) {
+    for (int s : kFftSizes)
+        if (s == n) return true;
+    return false;
+}
+
+// n = n1 * n2 with both factors register-DFT sizes, n1 >= n2, as balanced as possible.
+bool factor(int n, int *n1, int *n2) {
+    int best1 = -1, best2 = -1;
+    for (int a : kFftSizes) {
+        if (n % a) continue;
+        const int b = n / a;
+        if (!in_sizes(b) || a < b) continue;
+        if (best1 < 0 || a < best1) { best1 = a; best2 = b; }
+    }
+    if (best1 < 0) return false;
+    *n1 = best1;
+    *n2 = best2;
+    return true;
+}
+
+struct GridHost {
+    ibf_grid g;
+    std::vector<double> zf;
+    GridDev d;
+};
+
+struct ProfRec {
+    const char *name;
+    cudaEvent_t e0, e1;
+};
+
+}  // namespace
+
+struct ibf_plan {
+    int device = 0;
+    int ngrids = 0;
+    ibf_opts opts{};
+    int mixed = 0;
+    std::vector<GridHost> grids;
+    std::vector<void *> allocs;
+    Work work{};
+    size_t xsmem = 0, yzsmem = 0;
+    int nxblk = 0, nyzblk = 0, maxnz = 0;
+    long long ws_bytes = 0;
+    long long total_cells = 0;
+    cudaStream_t last_stream = nullptr;
+    // profiling
+    bool prof = false;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<const char *, std::pair<long long, double>>> prof_acc;
+};
+
+namespace {
+
+template <typename P> ibf_status dalloc(ibf_plan *pl, P **out, size_t bytes) {
+    static int fault_countdown = -2;
+    if (fault_countdown == -2) {
+        const char *f = getenv("IBF_FAULT_OOM_AT");  // test hook: fail the N-th plan allocation
+        fault_countdown = f ? atoi(f) : -1;
+    }
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (fault_countdown > 0 && --fault_countdown == 0) {
+        g_last_error = "injected allocation failure";
+        return IBF_ERR_OOM;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        g_last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return IBF_ERR_OOM;
+    }
+    pl->allocs.push_back(p);
+    pl->ws_bytes += (long long)bytes;
+    *out = static_cast<P *>(p);
+    return IBF_OK;
+}
+
+void free_all(ibf_plan *pl) {
+    for (void *p : pl->allocs) cudaFree(p);
+    pl->allocs.clear();
+    for (auto &r : pl->prof_pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    pl->prof_pending.clear();
+    for (auto e : pl->ev_pool) cudaEventDestroy(e);
+    pl->ev_pool.clear();
+}
+
+ibf_status validate(const ibf_grid *g, std::vector<double> &zf) {
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return IBF_ERR_INVALID_ARG;
+    if (!(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0)) return IBF_ERR_INVALID_ARG;
+    if (!std::isfinite(g->lx) || !std::isfinite(g->ly) || !std::isfinite(g->lz)) return IBF_ERR_INVALID_ARG;
+    if ((long long)g->nx * g->ny * g->nz > (1ll << 34)) return IBF_ERR_UNSUPPORTED_SIZE;
+    const int bcs[4] = {g->bc_x, g->bc_y, g->bc_zlo, g->bc_zhi};
+    for (int b : bcs)
+        if (b < IBF_BC_PERIODIC || b > IBF_BC_DIRICHLET) return IBF_ERR_INVALID_ARG;
+    if (g->bc_x != IBF_BC_PERIODIC || g->bc_y != IBF_BC_PERIODIC) return IBF_ERR_UNSUPPORTED_BC;
+    if (g->bc_zlo != IBF_BC_NEUMANN || g->bc_zhi != IBF_BC_NEUMANN) return IBF_ERR_UNSUPPORTED_BC;
+    int a, b;
+    if (!factor(g->nx, &a, &b) || !factor(g->ny, &a, &b)) return IBF_ERR_UNSUPPORTED_SIZE;
+    const int nz = g->nz;
+    zf.assign(nz + 1, 0.0);
+    if (g->zf) {
+        for (int k = 0; k <= nz; ++k) {
+            zf[k] = g->zf[k];
+            if (!std::isfinite(zf[k])) return IBF_ERR_INVALID_ARG;
+        }
+        if (std::fabs(zf[0]) > 1e-12 * g->lz || std::fabs(zf[nz] - g->lz) > 1e-12 * g->lz) return IBF_ERR_INVALID_ARG;
+        for (int k = 0; k < nz; ++k)
+            if (!(zf[k + 1] > zf[k])) return IBF_ERR_INVALID_ARG;
+    } else {
+        if (!std::isfinite(g->beta) || g->beta < 0) return IBF_ERR_INVALID_ARG;
+        for (int k = 0; k <= nz; ++k)
+            zf[k] = (g->beta == 0.0) ? g->lz * (double)k / nz
+                                     : 0.5 * g->lz * (1.0 + std::tanh(g->beta * (2.0 * k / nz - 1.0)) / std::tanh(g->beta));
+        for (int k = 0; k < nz; ++k)
+            if (!(zf[k + 1] > zf[k])) return IBF_ERR_INVALID_ARG;  // beta so large that faces collapse
+    }
+    zf[0] = 0.0;
+    zf[nz] = g->lz;
+    return IBF_OK;
+}
+
+// exp(-2 pi i r / n), r < n, in fp64 (host libm)
+void twiddles(int n, std::vector<double> &out) {
+    out.resize(2 * (size_t)n);
+    for (int r = 0; r < n; ++r) {
+        const double a = 2.0 * M_PI * (double)r / (double)n;
+        out[2 * r] = std::cos(a);
+        out[2 * r + 1] = -std::sin(a);
+    }
+}
+
+ibf_status upload(const void *host, void *dev, size_t bytes) {
+    cudaError_t e = cudaMemcpy(dev, host, bytes, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? IBF_OK : cuda_fail(e, "cudaMemcpy");
+}
+
+#define IBF_TRY(x) do { ibf_status _s = (x); if (_s != IBF_OK) return _s; } while (0)
+
+ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
+    const int mixed = pl->mixed;
+    const size_t csz = mixed ? 8 : 16;   // complex element bytes
+    const size_t rsz = mixed ? 4 : 8;    // real element bytes
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, pl->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    const int nsm = prop.multiProcessorCount;
+
+    pl->grids.resize(ngrids);
+    long long total_cols = 0;
+    for (int g = 0; g < ngrids; ++g) total_cols += grids[g].nx / 2 + 1;
+
+    long long spec = 0, cells = 0;
+    int zoff = 0, poff = 0, xblk = 0, yzblk = 0;
+    std::vector<double> twx_all, twy_all, tmp;
+    size_t maxx = 0, maxyz = 0;
+    for (int g = 0; g < ngrids; ++g) {
+        GridHost &H = pl->grids[g];
+        H.g = grids[g];
+        IBF_TRY(validate(&grids[g], H.zf));
+        H.g.zf = nullptr;
+        GridDev &d = H.d;
+        memset(&d, 0, sizeof(d));
+        d.nx = H.g.nx; d.ny = H.g.ny; d.nz = H.g.nz;
+        d.nxh = d.nx / 2 + 1;
+        factor(d.nx, &d.nx1, &d.nx2);
+        factor(d.ny, &d.ny1, &d.ny2);
+        // y-FFT + tridiagonal column blocks: at most 4096 modes per CTA (shared-memory state),
+        // enough blocks overall to fill the GPU twice.
+        const int mbmax = std::max(1, std::min(d.nxh, 4096 / d.ny));
+        int mb = (int)std::min<long long>(mbmax, std::max<long long>(1, total_cols / (2 * nsm)));
+        d.mb = mb;
+        d.ncb = (d.nxh + mb - 1) / mb;
+        // x kernels: rows/2 complex sequences of length nx per CTA, ~64 KB of shared memory
+        const int target = mixed ? 8192 : 4096;
+        int rows = 2 * std::max(1, target / d.nx);
+        const int ny_even = (d.ny + 1) & ~1;
+        rows = std::min(rows, ny_even);
+        d.rows = std::max(2, rows);
+        d.nrb = (d.ny + d.rows - 1) / d.rows;
+        d.spec_off = spec;
+        spec += (long long)d.nz * d.ncb * d.ny * d.mb;
+        d.cell_off = cells;
+        cells += (long long)d.nx * d.ny * d.nz;
+        d.tab_off = d.spec_off;
+        d.z_off = zoff;
+        zoff += d.nz + 1;
+        d.part_off = poff;
+        poff += d.nz * d.nrb;
+        d.twx_off = (int)(twx_all.size() / 2);
+        twiddles(d.nx, tmp);
+        twx_all.insert(twx_all.end(), tmp.begin(), tmp.end());
+        d.twy_off = (int)(twy_all.size() / 2);
+        twiddles(d.ny, tmp);
+        twy_all.insert(twy_all.end(), tmp.begin(), tmp.end());
+        d.xblk_off = xblk;
+        xblk += d.nz * d.nrb;
+        d.yzblk_off = yzblk;
+        yzblk += d.ncb;
+        d.dx = H.g.lx / d.nx; d.dy = H.g.ly / d.ny;
+        d.rdx = 1.0 / d.dx; d.rdy = 1.0 / d.dy;
+        d.inv_nxy = 1.0 / ((double)d.nx * d.ny);
+        d.sum_hz = H.zf[d.nz] - H.zf[0];
+        maxx = std::max(maxx, (size_t)(d.rows / 2) * (size_t)(d.nx1 * (d.nx2 + 1)) * csz);
+        maxyz = std::max(maxyz, (size_t)d.mb * (size_t)(d.ny1 * (d.ny2 + 1) + 1) * csz + (size_t)d.ny * d.mb * csz);
+        pl->maxnz = std::max(pl->maxnz, d.nz);
+        pl->total_cells += (long long)d.nx * d.ny * d.nz;
+    }
+    if (maxx > (size_t)prop.sharedMemPerBlockOptin || maxyz > (size_t)prop.sharedMemPerBlockOptin ||
+        (size_t)pl->maxnz * 8 > (size_t)prop.sharedMemPerBlockOptin)
+        return IBF_ERR_UNSUPPORTED_SIZE;
+    pl->xsmem = maxx;
+    pl->yzsmem = maxyz;
+    pl->nxblk = xblk;
+    pl->nyzblk = yzblk;
+
+    // per-level arrays
+    const int nzt = zoff;
+    std::vector<double> hz(nzt, 0.0), rhz(nzt, 0.0), rgzf(nzt, 0.0), az(nzt, 0.0), cz(nzt, 0.0), inv00(nzt, 0.0);
+    std::vector<float> azf(nzt), czf(nzt);
+    std::vector<float> rhz_df(2 * nzt), rgzf_df(2 * nzt);
+    for (int g = 0; g < ngrids; ++g) {
+        const GridHost &H = pl->grids[g];
+        const int nz = H.d.nz, o = H.d.z_off;
+        const std::vector<double> &zf = H.zf;
+        for (int k = 0; k < nz; ++k) { hz[o + k] = zf[k + 1] - zf[k]; rhz[o + k] = 1.0 / hz[o + k]; }
+        for (int k = 1; k < nz; ++k) {
+            const double gz = 0.5 * (zf[k] + zf[k + 1]) - 0.5 * (zf[k - 1] + zf[k]);
+            rgzf[o + k] = 1.0 / gz;
+        }
+        for (int k = 0; k < nz; ++k) {
+            az[o + k] = rhz[o + k] * rgzf[o + k];
+            cz[o + k] = rhz[o + k] * rgzf[o + k + 1];
+        }
+        // pinned (0,0) system: level 0 fixed to zero
+        double cp = 0.0;
+        inv00[o] = 0.0;
+        for (int k = 1; k < nz; ++k) {
+            inv00[o + k] = 1.0 / (-(az[o + k] + cz[o + k]) - az[o + k] * cp);
+            cp = cz[o + k] * inv00[o + k];
+        }
+        for (int k = 0; k <= nz; ++k) {
+            azf[o + k] = (float)az[o + k];
+            czf[o + k] = (float)cz[o + k];
+            float h = (float)rhz[o + k];
+            rhz_df[2 * (o + k)] = h;
+            rhz_df[2 * (o + k) + 1] = (float)(rhz[o + k] - (double)h);
+            h = (float)rgzf[o + k];
+            rgzf_df[2 * (o + k)] = h;
+            rgzf_df[2 * (o + k) + 1] = (float)(rgzf[o + k] - (double)h);
+        }
+    }
+
+    // device allocations
+    Work &w = pl->work;
+    w.ngrids = ngrids;
+    GridDev *dgrids;
+    IBF_TRY(dalloc(pl, &dgrids, sizeof(GridDev) * ngrids));
+    w.grids = dgrids;
+    int *dx, *dyz;
+    IBF_TRY(dalloc(pl, &dx, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(dalloc(pl, &dyz, sizeof(int) * (ngrids + 1)));
+    w.xblk_start = dx;
+    w.yzblk_start = dyz;
+    IBF_TRY(dalloc(pl, &w.z.hz, sizeof(double) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.rhz, sizeof(double) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.rgzf, sizeof(double) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.az, sizeof(double) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.cz, sizeof(double) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.inv00, sizeof(double) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.azf, sizeof(float) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.czf, sizeof(float) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.rhz_df, sizeof(float2) * nzt));
+    IBF_TRY(dalloc(pl, &w.z.rgzf_df, sizeof(float2) * nzt));
+    IBF_TRY(dalloc(pl, &w.spec, csz * (size_t)spec));
+    IBF_TRY(dalloc(pl, &w.tab, rsz * (size_t)spec));
+    void *twx, *twy;
+    IBF_TRY(dalloc(pl, &twx, csz * twx_all.size() / 2));
+    IBF_TRY(dalloc(pl, &twy, csz * twy_all.size() / 2));
+    w.twx = twx;
+    w.twy = twy;
+    if (mixed) IBF_TRY(dalloc(pl, &w.bdf, sizeof(float2) * (size_t)cells));
+    IBF_TRY(dalloc(pl, &w.phi_ws, sizeof(double) * (size_t)cells));
+    IBF_TRY(dalloc(pl, &w.partial, sizeof(double) * (size_t)std::max(poff, 1)));
+    IBF_TRY(dalloc(pl, &w.partial_phi, sizeof(double) * (size_t)std::max(poff, 1)));
+    IBF_TRY(dalloc(pl, &w.mean_b, sizeof(double) * ngrids));
+    IBF_TRY(dalloc(pl, &w.maxb, sizeof(unsigned long long) * ngrids));
+    IBF_TRY(dalloc(pl, &w.maxdiv, sizeof(unsigned long long) * ngrids));
+    IBF_TRY(dalloc(pl, &w.err, sizeof(unsigned)));
+
+    std::vector<GridDev> hd(ngrids);
+    std::vector<int> xs(ngrids + 1), ys(ngrids + 1);
+    for (int g = 0; g < ngrids; ++g) {
+        hd[g] = pl->grids[g].d;
+        xs[g] = hd[g].xblk_off;
+        ys[g] = hd[g].yzblk_off;
+    }
+    xs[ngrids] = xblk;
+    ys[ngrids] = yzblk;
+    IBF_TRY(upload(hd.data(), dgrids, sizeof(GridDev) * ngrids));
+    IBF_TRY(upload(xs.data(), dx, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(upload(ys.data(), dyz, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(upload(hz.data(), w.z.hz, sizeof(double) * nzt));
+    IBF_TRY(upload(rhz.data(), w.z.rhz, sizeof(double) * nzt));
+    IBF_TRY(upload(rgzf.data(), w.z.rgzf, sizeof(double) * nzt));
+    IBF_TRY(upload(az.data(), w.z.az, sizeof(double) * nzt));
+    IBF_TRY(upload(cz.data(), w.z.cz, sizeof(double) * nzt));
+    IBF_TRY(upload(inv00.data(), w.z.inv00, sizeof(double) * nzt));
+    IBF_TRY(upload(azf.data(), w.z.azf, sizeof(float) * nzt));
+    IBF_TRY(upload(czf.data(), w.z.czf, sizeof(float) * nzt));
+    IBF_TRY(upload(rhz_df.data(), w.z.rhz_df, sizeof(float2) * nzt));
+    IBF_TRY(upload(rgzf_df.data(), w.z.rgzf_df, sizeof(float2) * nzt));
+    if (mixed) {
+        std::vector<float> fx(twx_all.begin(), twx_all.end()), fy(twy_all.begin(), twy_all.end());
+        IBF_TRY(upload(fx.data(), twx, sizeof(float) * fx.size()));
+        IBF_TRY(upload(fy.data(), twy, sizeof(float) * fy.size()));
+    } else {
+        IBF_TRY(upload(twx_all.data(), twx, sizeof(double) * twx_all.size()));
+        IBF_TRY(upload(twy_all.data(), twy, sizeof(double) * twy_all.size()));
+    }
+    e = cudaMemset(w.spec, 0, csz * (size_t)spec);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    e = cudaMemset(w.err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    e = cudaMemset(w.mean_b, 0, sizeof(double) * ngrids);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+
+    e = set_smem_limits(mixed, pl->xsmem, pl->yzsmem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    e = launch_build_table(mixed, w, pl->nyzblk, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "pivot table kernel");
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "pivot table kernel");
+    return IBF_OK;
+}
+
+// ------------------------------------------------------------ call sequencing
+struct Ctx {
+    ibf_plan *pl;
+    cudaStream_t st;
+};
+
+cudaEvent_t get_event(ibf_plan *pl) {
+    if (!pl->ev_pool.empty()) {
+        cudaEvent_t e = pl->ev_pool.back();
+        pl->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <typename F> ibf_status timed(Ctx &c, const char *name, F f) {
+    ProfRec r{name, nullptr, nullptr};
+    if (c.pl->prof) {
+        r.e0 = get_event(c.pl);
+        r.e1 = get_event(c.pl);
+        cudaEventRecord(r.e0, c.st);
+    }
+    cudaError_t e = f();
+    if (c.pl->prof) {
+        cudaEventRecord(r.e1, c.st);
+        c.pl->prof_pending.push_back(r);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    return IBF_OK;
+}
+
+// Fill user pointers for grids [g0, g1).
+void fill_ptrs(ibf_plan *pl, UserPtrs &p, int g0, int g1, const ibf_fields *in, const ibf_fields *out) {
+    memset(&p, 0, sizeof(p));
+    p.g0 = g0;
+    p.g1 = g1;
+    p.blk0 = pl->grids[g0].d.xblk_off;
+    for (int g = g0; g < g1; ++g) {
+        const int i = g - g0;
+        if (in) { p.in_u[i] = in[g].u; p.in_v[i] = in[g].v; p.in_w[i] = in[g].w; p.in_p[i] = in[g].p; }
+        if (out) { p.out_u[i] = out[g].u; p.out_v[i] = out[g].v; p.out_w[i] = out[g].w; p.out_p[i] = out[g].p; }
+    }
+}
+
+int chunk_blocks(ibf_plan *pl, int g0, int g1) {
+    const int b0 = pl->grids[g0].d.xblk_off;
+    const int b1 = (g1 < pl->ngrids) ? pl->grids[g1].d.xblk_off : pl->nxblk;
+    return b1 - b0;
+}
+
+// x-kernel launches over chunks of grids (user pointers travel as launch parameters)
+template <typename F>
+ibf_status for_chunks(Ctx &c, const char *name, const ibf_fields *in, const ibf_fields *out, F f) {
+    for (int g0 = 0; g0 < c.pl->ngrids; g0 += kGridsPerLaunch) {
+        const int g1 = std::min(c.pl->ngrids, g0 + kGridsPerLaunch);
+        UserPtrs p;
+        fill_ptrs(c.pl, p, g0, g1, in, out);
+        const int nb = chunk_blocks(c.pl, g0, g1);
+        IBF_TRY(timed(c, name, [&]() { return f(p, nb); }));
+    }
+    return IBF_OK;
+}
+
+// One solve S^-1 of the right-hand side already transformed into the spectrum.
+ibf_status solve_core(Ctx &c, int first) {
+    ibf_plan *pl = c.pl;
+    const Work &w = pl->work;
+    IBF_TRY(timed(c, "yz_forward", [&]() { return launch_yzfwd(pl->mixed, w, pl->nyzblk, pl->yzsmem, c.st); }));
+    IBF_TRY(timed(c, "mode00", [&]() { return launch_k00(w, pl->mixed, first, pl->maxnz, c.st); }));
+    IBF_TRY(timed(c, "yz_backward", [&]() { return launch_yzbwd(pl->mixed, w, pl->nyzblk, pl->yzsmem, c.st); }));
+    return IBF_OK;
+}
+
+ibf_status run(ibf_plan *pl, const ibf_fields *in, const ibf_fields *out, double dt, double alpha,
+               const ibf_stats *stats, cudaStream_t st, int adjoint) {
+    Ctx c{pl, st};
+    const Work &w = pl->work;
+    const double s = alpha * dt, rs = 1.0 / s;
+    const int mixed = pl->mixed;
+    const int use_ws = adjoint ? 1 : 0;
+    cudaError_t e = cudaMemsetAsync(w.maxb, 0, sizeof(unsigned long long) * pl->ngrids, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.maxdiv, 0, sizeof(unsigned long long) * pl->ngrids, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const int xmode = adjoint ? XM_ADJ : XM_DIV;
+    IBF_TRY(for_chunks(c, adjoint ? "x_forward_adjoint_rhs" : "x_forward_div", in, out, [&](const UserPtrs &p, int nb) {
+        return launch_xfwd(mixed, xmode, w, p, use_ws, nb, s, rs, pl->xsmem, st);
+    }));
+    IBF_TRY(solve_core(c, 1));
+    IBF_TRY(for_chunks(c, "x_inverse_store", in, out, [&](const UserPtrs &p, int nb) {
+        return launch_xinv(mixed, IM_STORE, w, p, use_ws, nb, pl->xsmem, st);
+    }));
+    if (mixed) {
+        for (int r = 0; r < pl->opts.refine_steps; ++r) {
+            IBF_TRY(for_chunks(c, "x_forward_residual", in, out, [&](const UserPtrs &p, int nb) {
+                return launch_xfwd(mixed, XM_RESID, w, p, use_ws, nb, s, rs, pl->xsmem, st);
+            }));
+            IBF_TRY(solve_core(c, 0));
+            IBF_TRY(for_chunks(c, "x_inverse_accumulate", in, out, [&](const UserPtrs &p, int nb) {
+                return launch_xinv(mixed, IM_ACCUM, w, p, use_ws, nb, pl->xsmem, st);
+            }));
+        }
+    }
+    IBF_TRY(for_chunks(c, adjoint ? "correct_adjoint" : "correct", in, out, [&](const UserPtrs &p, int nb) {
+        return launch_correct(mixed, adjoint, w, p, use_ws, nb, s, st);
+    }));
+    if (!adjoint && stats && (stats->max_div || stats->max_div_in || stats->compat)) {
+        if (stats->max_div) {
+            IBF_TRY(for_chunks(c, "divergence_stat", in, out, [&](const UserPtrs &p, int nb) {
+                return launch_divstat(mixed, w, p, nb, st);
+            }));
+        }
+        IBF_TRY(timed(c, "finalize", [&]() {
+            return launch_finalize(w, stats->max_div, stats->max_div_in, stats->compat, s, st);
+        }));
+    }
+    pl->last_stream = st;
+    return IBF_OK;
+}
+
+bool fields_ok(const ibf_fields *f, int n, bool need_p) {
+    if (!f) return false;
+    for (int g = 0; g < n; ++g) {
+        if (!f[g].u || !f[g].v || !f[g].w) return false;
+        if (need_p && !f[g].p) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ibf_status_string(ibf_status s) {
+    switch (s) {
+        case IBF_OK: return "ok";
+        case IBF_ERR_INVALID_ARG: return "invalid argument";
+        case IBF_ERR_UNSUPPORTED_SIZE: return "unsupported grid size";
+        case IBF_ERR_OOM: return "device allocation failed";
+        case IBF_ERR_CUDA: return "CUDA runtime error";
+        case IBF_ERR_TIMEOUT: return "bounded device wait timed out";
+        case IBF_ERR_NONFINITE: return "non-finite value in the right-hand side";
+        case IBF_WARN_INCOMPATIBLE_RHS: return "right-hand side incompatible with the Neumann walls (mean removed)";
+        case IBF_ERR_UNSUPPORTED_BC: return "unsupported boundary condition";
+    }
+    return "unknown status";
+}
+
+const char *ibf_last_error(void) { return g_last_error.c_str(); }
+
+ibf_status ibf_projection_plan(ibf_plan **plan, const ibf_grid *grids, int ngrids, const ibf_opts *opts, int device) {
+    if (!plan) return IBF_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!grids || !opts || ngrids < 1 || ngrids > IBF_MAX_GRIDS || device < 0) return IBF_ERR_INVALID_ARG;
+    if (opts->precision != IBF_FP64 && opts->precision != IBF_MIXED) return IBF_ERR_INVALID_ARG;
+    if (opts->refine_steps < 0 || opts->refine_steps > 8 || opts->reserved != 0) return IBF_ERR_INVALID_ARG;
+    if (opts->precision == IBF_FP64 && opts->refine_steps != 0) return IBF_ERR_INVALID_ARG;
+    // host-side validation of every grid before touching the device
+    for (int g = 0; g < ngrids; ++g) {
+        std::vector<double> zf;
+        ibf_status s = validate(&grids[g], zf);
+        if (s != IBF_OK) return s;
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    ibf_plan *pl = new (std::nothrow) ibf_plan();
+    if (!pl) return IBF_ERR_OOM;
+    pl->device = device;
+    pl->ngrids = ngrids;
+    pl->opts = *opts;
+    pl->mixed = opts->precision == IBF_MIXED;
+    ibf_status s = build_plan(pl, grids, ngrids);
+    if (s != IBF_OK) {
+        cudaDeviceSynchronize();
+        free_all(pl);
+        delete pl;
+        return s;
+    }
+    *plan = pl;
+    return IBF_OK;
+}
+
+ibf_status ibf_project(ibf_plan *plan, const ibf_fields *in, const ibf_fields *out, double dt, double alpha,
+                       const ibf_stats *stats, void *stream) {
+    if (!plan || !fields_ok(in, plan->ngrids, false) || !fields_ok(out, plan->ngrids, true)) return IBF_ERR_INVALID_ARG;
+    if (!(dt > 0) || !(alpha > 0) || !std::isfinite(dt) || !std::isfinite(alpha)) return IBF_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return run(plan, in, out, dt, alpha, stats, static_cast<cudaStream_t>(stream), 0);
+}
+
+ibf_status ibf_project_backward(ibf_plan *plan, const ibf_fields *grad_out, const ibf_fields *grad_in, double dt,
+                                double alpha, void *stream) {
+    if (!plan || !fields_ok(grad_out, plan->ngrids, false) || !fields_ok(grad_in, plan->ngrids, false))
+        return IBF_ERR_INVALID_ARG;
+    if (!(dt > 0) || !(alpha > 0) || !std::isfinite(dt) || !std::isfinite(alpha)) return IBF_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return run(plan, grad_out, grad_in, dt, alpha, nullptr, static_cast<cudaStream_t>(stream), 1);
+}
+
+ibf_status ibf_plan_sync_status(ibf_plan *plan) {
+    if (!plan) return IBF_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(plan->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned word = 0;
+    e = cudaMemcpy(&word, plan->work.err, sizeof(word), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(plan->work.err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    if (word & (1u << IBF_ERR_TIMEOUT)) return IBF_ERR_TIMEOUT;
+    if (word & (1u << IBF_ERR_NONFINITE)) return IBF_ERR_NONFINITE;
+    if (word & (1u << IBF_WARN_INCOMPATIBLE_RHS)) return IBF_WARN_INCOMPATIBLE_RHS;
+    return IBF_OK;
+}
+
+ibf_status ibf_plan_destroy(ibf_plan *plan) {
+    if (!plan) return IBF_OK;
+    cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    free_all(plan);
+    delete plan;
+    return IBF_OK;
+}
+
+ibf_status ibf_plan_get_info(const ibf_plan *plan, ibf_plan_info *info) {
+    if (!plan || !info) return IBF_ERR_INVALID_ARG;
+    info->workspace_bytes = plan->ws_bytes;
+    info->ngrids = plan->ngrids;
+    info->precision = plan->opts.precision;
+    info->refine_steps = plan->opts.refine_steps;
+    info->total_cells = plan->total_cells;
+    return IBF_OK;
+}
+
+ibf_status ibf_profile_enable(ibf_plan *plan, int enable) {
+    if (!plan) return IBF_ERR_INVALID_ARG;
+    plan->prof = enable != 0;
+    return IBF_OK;
+}
+
+static void prof_collect(ibf_plan *plan) {
+    if (plan->prof_pending.empty()) return;
+    cudaSetDevice(plan->device);
+    cudaEventSynchronize(plan->prof_pending.back().e1);
+    for (auto &r : plan->prof_pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        bool found = false;
+        for (auto &a : plan->prof_acc)
+            if (strcmp(a.first, r.name) == 0) { a.second.first += 1; a.second.second += ms; found = true; break; }
+        if (!found) plan->prof_acc.push_back({r.name, {1, (double)ms}});
+        plan->ev_pool.push_back(r.e0);
+        plan->ev_pool.push_back(r.e1);
+    }
+    plan->prof_pending.clear();
+}
+
+int ibf_profile_read(ibf_plan *plan, const char **names, long long *launches, double *ms, int cap) {
+    if (!plan) return 0;
+    prof_collect(plan);
+    int n = 0;
+    for (auto &a : plan->prof_acc) {
+        if (n >= cap) break;
+        if (names) names[n] = a.first;
+        if (launches) launches[n] = a.second.first;
+        if (ms) ms[n] = a.second.second;
+        ++n;
+    }
+    return n;
+}
+
+ibf_status ibf_profile_reset(ibf_plan *plan) {
+    if (!plan) return IBF_ERR_INVALID_ARG;
+    prof_collect(plan);
+    plan->prof_acc.clear();
+    return IBF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,405 @@
+// ibf_device.cuh -- device building blocks of the projection kernels:
+//   * complex arithmetic,
+//   * float-float ("df32", an unevaluated sum hi + lo of two fp32 numbers) arithmetic
+//     after Dekker (1971) and Knuth's TwoSum, with FMA-based exact products,
+//   * fp64 <-> df32 / fp32 conversions done with integer bit operations only
+//     (GB300 runs fp64 arithmetic and F2F conversions at ~1/72 of the fp32 rate),
+//   * register DFTs of length 1..32 (mixed radix 2/3/4 Stockham autosort stages,
+//     Govindaraju et al., SC 2008) and a two-level shared-memory FFT built on them.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ibf {
+
+// ------------------------------------------------------------------ complex
+template <typename T> struct cx { T x, y; };
+
+template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {  // a * conj(b)
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.x * s, a.y * s}; }
+template <typename T> __device__ __forceinline__ cx<T> cconj(cx<T> a) { return {a.x, -a.y}; }
+
+// ------------------------------------------------------------------ float-float
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ df df_make(float a) { return {a, 0.f}; }
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_addf(df a, float b) {
+    df s = two_sum(a.hi, b);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mulf(df a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ float df_to_f(df a) { return __fadd_rn(a.hi, a.lo); }
+
+// fp64 -> df32 without fp64 arithmetic.  hi takes the sign, the exponent and the
+// top 23 fraction bits (truncated); lo = x - hi is formed from the remaining 29
+// bits (rounded to 24 by the integer->float conversion), so hi + lo == x within
+// 2^-48 relative.  |x| < 2^-74 loses lo, |x| < 2^-126 flushes to 0, |x| >= 2^128
+// maps to +-inf, NaN stays NaN.
+__device__ __forceinline__ df f64_to_df(double x) {
+    const unsigned long long X = (unsigned long long)__double_as_longlong(x);
+    const unsigned h = (unsigned)(X >> 32), l = (unsigned)X;
+    const unsigned e = (h >> 20) & 0x7FFu;
+    const unsigned s = h & 0x80000000u;
+    unsigned hbits = __funnelshift_l(l, (h & 0x7FFFFFFFu) - (896u << 20), 3);
+    float scale = __uint_as_float(s | ((e - 948u) << 23));
+    float lo = __fmul_rn(__uint2float_rn(l & 0x1FFFFFFFu), scale);
+    if (e < 949u) {
+        lo = 0.f;
+        if (e < 897u) hbits = 0u;
+    }
+    if (e > 1150u) {
+        hbits = 0x7F800000u | (((e == 2047u) && ((h & 0xFFFFFu) | l)) ? 0x400000u : 0u);
+        lo = 0.f;
+    }
+    return {__uint_as_float(s | hbits), lo};
+}
+
+// fp32 -> fp64 bit pattern without F2F (fp32 denormals flush to signed zero).
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)s);
+    unsigned long long E = (e == 0xFFu) ? 0x7FFull : (unsigned long long)(e + 896u);
+    unsigned long long M = (unsigned long long)(b & 0x7FFFFFu) << 29;
+    return __longlong_as_double((long long)(s | (E << 52) | M));
+}
+
+// df32 -> fp64 without fp64 arithmetic: the two 24-bit significands are
+// aligned in a 64-bit integer and added; the result is truncated to 53 bits.
+__device__ __forceinline__ double df_to_f64(df a) {
+    const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
+    const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
+    if (eh == 0) return f32_to_f64(a.lo);          // hi == 0 (or denormal): lo carries the value
+    if (eh == 0xFF) return f32_to_f64(a.hi);       // inf / nan
+    unsigned long long M = (1ull << 52) | ((unsigned long long)(hb & 0x7FFFFFu) << 29);
+    if (el != 0) {
+        const unsigned long long L = (1ull << 23) | (unsigned long long)(lb & 0x7FFFFFu);
+        const int sh = 29 - (eh - el);               // left shift of L into M's units
+        unsigned long long Ls = 0ull;
+        if (sh >= 0) Ls = L << (sh > 40 ? 40 : sh);
+        else if (sh > -40) Ls = L >> (-sh);
+        if ((hb ^ lb) & 0x80000000u) M -= Ls; else M += Ls;
+    }
+    int E = eh + 896;
+    if (M >> 53) { M >>= 1; E += 1; }
+    else if (!(M >> 52)) {
+        if (M == 0ull) return __longlong_as_double((long long)((unsigned long long)(hb & 0x80000000u) << 32));
+        const int lz = __clzll((long long)M) - 11;
+        M <<= lz; E -= lz;
+    }
+    return __longlong_as_double((long long)(((unsigned long long)(hb & 0x80000000u) << 32) |
+                                            ((unsigned long long)E << 52) | (M & ((1ull << 52) - 1))));
+}
+
+// ------------------------------------------------------------------ precision policies
+// FP64 path: everything in double.  MIXED path: transforms in float, stencils in df32.
+struct F64Arith {
+    typedef double V;      // high-precision value
+    __device__ __forceinline__ static V load(double x) { return x; }
+    __device__ __forceinline__ static double store(V v) { return v; }
+    __device__ __forceinline__ static V add(V a, V b) { return a + b; }
+    __device__ __forceinline__ static V sub(V a, V b) { return a - b; }
+    __device__ __forceinline__ static V mul(V a, V b) { return a * b; }
+    __device__ __forceinline__ static V from_f(float a) { return (double)a; }
+    __device__ __forceinline__ static V zero() { return 0.0; }
+};
+struct DFArith {
+    typedef df V;
+    __device__ __forceinline__ static V load(double x) { return f64_to_df(x); }
+    __device__ __forceinline__ static double store(V v) { return df_to_f64(v); }
+    __device__ __forceinline__ static V add(V a, V b) { return df_add(a, b); }
+    __device__ __forceinline__ static V sub(V a, V b) { return df_sub(a, b); }
+    __device__ __forceinline__ static V mul(V a, V b) { return df_mul(a, b); }
+    __device__ __forceinline__ static V from_f(float a) { return df_make(a); }
+    __device__ __forceinline__ static V zero() { return df_make(0.f); }
+};
+
+// ------------------------------------------------------------------ twiddle constants
+// exp(-2 pi i r / 96): every twiddle inside a register DFT of length dividing 96.
+__constant__ double c_tw96d[96][2] = {
+#include "tw96.inc"
+};
+__constant__ float c_tw96f[96][2] = {
+#include "tw96.inc"
+};
+
+template <typename T> struct Tw96;
+template <> struct Tw96<double> {
+    __device__ __forceinline__ static cx<double> get(int r) { return {c_tw96d[r][0], c_tw96d[r][1]}; }
+};
+template <> struct Tw96<float> {
+    __device__ __forceinline__ static cx<float> get(int r) { return {c_tw96f[r][0], c_tw96f[r][1]}; }
+};
+
+// ------------------------------------------------------------------ butterflies
+// DIR = -1: forward (exp(-i ...)), DIR = +1: inverse (unnormalised).
+template <typename T, int R, int DIR> struct Bfly;
+template <typename T, int DIR> struct Bfly<T, 2, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *v) {
+        cx<T> a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+template <typename T, int DIR> struct Bfly<T, 3, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *v) {
+        const T c = (T)0.86602540378443864676;  // sin(2 pi / 3)
+        cx<T> s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        cx<T> t = {v[0].x - (T)0.5 * s.x, v[0].y - (T)0.5 * s.y};
+        v[0] = cadd(v[0], s);
+        // v1 = t + DIR*i*c*d, v2 = t - DIR*i*c*d  with i*d = (-d.y, d.x)
+        v[1] = {t.x - (T)DIR * c * d.y, t.y + (T)DIR * c * d.x};
+        v[2] = {t.x + (T)DIR * c * d.y, t.y - (T)DIR * c * d.x};
+    }
+};
+template <typename T, int DIR> struct Bfly<T, 4, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *v) {
+        cx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        cx<T> t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+        cx<T> it3 = {(T)(-DIR) * t3.y, (T)DIR * t3.x};  // (DIR*i) * t3
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, it3);
+        v[3] = csub(t1, it3);
+    }
+};
+
+// One Stockham autosort stage of radix R over P registers; NS = product of the
+// radices of the previous stages.  Output in natural order after the last stage.
+template <typename T, int P, int R, int NS, int DIR>
+__device__ __forceinline__ void stockham_stage(const cx<T> *x, cx<T> *y) {
+#pragma unroll
+    for (int j = 0; j < P / R; ++j) {
+        const int k = j % NS;
+        cx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            v[r] = x[j + r * (P / R)];
+            if (NS > 1 && r > 0 && k > 0) {
+                cx<T> w = Tw96<T>::get((r * k * (96 / (NS * R))) % 96);
+                if (DIR > 0) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        Bfly<T, R, DIR>::run(v);
+        const int idx = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) y[idx + r * NS] = v[r];
+    }
+}
+
+// Register DFT of length P (in place on x[0..P-1]).
+template <typename T, int P, int DIR> struct RegDFT;
+template <typename T, int DIR> struct RegDFT<T, 1, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *) {}
+};
+template <typename T, int DIR> struct RegDFT<T, 2, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) { Bfly<T, 2, DIR>::run(x); }
+};
+template <typename T, int DIR> struct RegDFT<T, 3, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) { Bfly<T, 3, DIR>::run(x); }
+};
+template <typename T, int DIR> struct RegDFT<T, 4, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) { Bfly<T, 4, DIR>::run(x); }
+};
+template <typename T, int DIR> struct RegDFT<T, 6, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) {
+        cx<T> y[6];
+        stockham_stage<T, 6, 2, 1, DIR>(x, y);
+        stockham_stage<T, 6, 3, 2, DIR>(y, x);
+    }
+};
+template <typename T, int DIR> struct RegDFT<T, 8, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) {
+        cx<T> y[8];
+        stockham_stage<T, 8, 4, 1, DIR>(x, y);
+        stockham_stage<T, 8, 2, 4, DIR>(y, x);
+    }
+};
+template <typename T, int DIR> struct RegDFT<T, 12, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) {
+        cx<T> y[12];
+        stockham_stage<T, 12, 4, 1, DIR>(x, y);
+        stockham_stage<T, 12, 3, 4, DIR>(y, x);
+    }
+};
+template <typename T, int DIR> struct RegDFT<T, 16, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) {
+        cx<T> y[16];
+        stockham_stage<T, 16, 4, 1, DIR>(x, y);
+        stockham_stage<T, 16, 4, 4, DIR>(y, x);
+    }
+};
+template <typename T, int DIR> struct RegDFT<T, 24, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) {
+        cx<T> y[24];
+        stockham_stage<T, 24, 4, 1, DIR>(x, y);
+        stockham_stage<T, 24, 2, 4, DIR>(y, x);
+        stockham_stage<T, 24, 3, 8, DIR>(x, y);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) x[i] = y[i];
+    }
+};
+template <typename T, int DIR> struct RegDFT<T, 32, DIR> {
+    __device__ __forceinline__ static void run(cx<T> *x) {
+        cx<T> y[32];
+        stockham_stage<T, 32, 4, 1, DIR>(x, y);
+        stockham_stage<T, 32, 4, 4, DIR>(y, x);
+        stockham_stage<T, 32, 2, 16, DIR>(x, y);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = y[i];
+    }
+};
+
+// ------------------------------------------------------------------ two-level smem FFT
+// A length-N sequence (N = N1 * N2) lives in shared memory as an N1 x (N2+1)
+// padded matrix: element (row r, col c) at base + r*(N2+1) + c.  The padding
+// keeps the strided row-pass accesses free of bank conflicts.
+//   forward:  input x[p] at (p / N2, p % N2)  [natural]
+//             column pass: DFT_N1 down each column, multiply (q1, p2) by w_N^(p2 q1)
+//             row pass:    DFT_N2 along each row
+//             output X[q] at (q % N1, q / N1)  ["transposed"]
+//   inverse:  input at the transposed positions, row pass (DFT_N2^-1), multiply by
+//             w_N^-(p2 q1), column pass (DFT_N1^-1); output natural, unnormalised.
+// tw[r] = exp(-2 pi i r / N), r < N (global memory, read through the L1 cache).
+__host__ __device__ __forceinline__ int fft_pos_nat(int p, int N2) { return (p / N2) * (N2 + 1) + (p % N2); }
+__host__ __device__ __forceinline__ int fft_pos_tr(int q, int N1, int N2) { return (q % N1) * (N2 + 1) + (q / N1); }
+__host__ __device__ __forceinline__ int fft_seq_len(int N1, int N2) { return N1 * (N2 + 1); }
+
+template <typename T> __device__ __forceinline__ cx<T> ld_tw(const cx<T> *tw, int r);
+template <> __device__ __forceinline__ cx<float> ld_tw<float>(const cx<float> *tw, int r) {
+    float2 v = __ldg(reinterpret_cast<const float2 *>(tw) + r);
+    return {v.x, v.y};
+}
+template <> __device__ __forceinline__ cx<double> ld_tw<double>(const cx<double> *tw, int r) {
+    double2 v = __ldg(reinterpret_cast<const double2 *>(tw) + r);
+    return {v.x, v.y};
+}
+
+// column task: DFT_N1 down column c of one sequence (P == N1); forward multiplies by w_N^(c q1)
+template <typename T, int P, int DIR>
+__device__ __forceinline__ void fft_col_task(cx<T> *seq, int c, int ld, const cx<T> *tw) {
+    cx<T> x[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) x[r] = seq[r * ld + c];
+    RegDFT<T, P, DIR>::run(x);
+    if (DIR < 0 && c > 0) {
+#pragma unroll
+        for (int r = 1; r < P; ++r) x[r] = cmul(x[r], ld_tw<T>(tw, c * r));
+    }
+#pragma unroll
+    for (int r = 0; r < P; ++r) seq[r * ld + c] = x[r];
+}
+// row task: DFT_N2 along row q1 of one sequence (P == N2); inverse then multiplies by w_N^-(p2 q1)
+template <typename T, int P, int DIR>
+__device__ __forceinline__ void fft_row_task(cx<T> *seq, int q1, int ld, const cx<T> *tw) {
+    cx<T> x[P];
+    cx<T> *row = seq + q1 * ld;
+#pragma unroll
+    for (int c = 0; c < P; ++c) x[c] = row[c];
+    RegDFT<T, P, DIR>::run(x);
+    if (DIR > 0 && q1 > 0) {
+#pragma unroll
+        for (int c = 1; c < P; ++c) x[c] = cmulc(x[c], ld_tw<T>(tw, c * q1));
+    }
+#pragma unroll
+    for (int c = 0; c < P; ++c) row[c] = x[c];
+}
+
+template <typename T, int P, int DIR>
+__device__ __forceinline__ void fft_col_pass_P(cx<T> *buf, int nseq, int sstride, int N2, const cx<T> *tw,
+                                               int tid, int nthr) {
+    const int ntask = nseq * N2;
+    for (int t = tid; t < ntask; t += nthr) {
+        const int s = t / N2, c = t - s * N2;
+        fft_col_task<T, P, DIR>(buf + (size_t)s * sstride, c, N2 + 1, tw);
+    }
+}
+template <typename T, int P, int DIR>
+__device__ __forceinline__ void fft_row_pass_P(cx<T> *buf, int nseq, int sstride, int N1, int N2, const cx<T> *tw,
+                                               int tid, int nthr) {
+    const int ntask = nseq * N1;
+    for (int t = tid; t < ntask; t += nthr) {
+        const int s = t / N1, q1 = t - s * N1;
+        fft_row_task<T, P, DIR>(buf + (size_t)s * sstride, q1, N2 + 1, tw);
+    }
+}
+
+#define IBF_FFT_SIZES(X) X(1) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32)
+
+template <typename T, int DIR>
+__device__ __forceinline__ void fft_col_pass(cx<T> *buf, int nseq, int sstride, int N1, int N2, const cx<T> *tw,
+                                          int tid, int nthr) {
+    switch (N1) {
+#define IBF_CASE(P) case P: fft_col_pass_P<T, P, DIR>(buf, nseq, sstride, N2, tw, tid, nthr); break;
+        IBF_FFT_SIZES(IBF_CASE)
+#undef IBF_CASE
+        default: break;
+    }
+}
+template <typename T, int DIR>
+__device__ __forceinline__ void fft_row_pass(cx<T> *buf, int nseq, int sstride, int N1, int N2, const cx<T> *tw,
+                                          int tid, int nthr) {
+    switch (N2) {
+#define IBF_CASE(P) case P: fft_row_pass_P<T, P, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr); break;
+        IBF_FFT_SIZES(IBF_CASE)
+#undef IBF_CASE
+        default: break;
+    }
+}
+
+// Batch of nseq sequences at buf + s * sstride.  Ends with a __syncthreads().
+template <typename T, int DIR>
+__device__ __forceinline__ void fft_batch(cx<T> *buf, int nseq, int sstride, int N1, int N2, const cx<T> *tw) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (DIR < 0) {
+        fft_col_pass<T, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr);
+        __syncthreads();
+        fft_row_pass<T, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr);
+    } else {
+        fft_row_pass<T, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr);
+        __syncthreads();
+        fft_col_pass<T, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr);
+    }
+    __syncthreads();
+}
+
+}  // namespace ibf

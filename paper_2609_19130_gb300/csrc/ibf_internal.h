@@ -1,0 +1,91 @@
+// ibf_internal.h -- plan-internal data shared by the host plan code (ibf_capi.cpp)
+// and the kernels (ibf_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ibf {
+
+// Largest number of grids whose user pointers travel in one launch's parameters.
+constexpr int kGridsPerLaunch = 32;
+// Thread counts of the kernels.
+constexpr int kXThreads = 256;   // x-direction (row) kernels and stencil kernels
+constexpr int kYZThreads = 128;  // y-FFT + z-tridiagonal column kernels
+
+// Per-grid descriptor, one entry per grid in device memory.
+struct GridDev {
+    int nx, ny, nz, nxh;       // cells; nxh = nx/2 + 1 x-modes kept by the real transform
+    int nx1, nx2, ny1, ny2;    // two-level FFT factors: nx = nx1*nx2, ny = ny1*ny2
+    int mb, ncb;               // x-modes per column block of the yz kernels, number of blocks
+    int rows, nrb;             // rows per CTA of the x kernels (even), row blocks per plane
+    long long spec_off;        // offset of the grid's spectrum (complex elements)
+    long long cell_off;        // offset of the grid's per-cell workspace (cells)
+    long long tab_off;         // offset of the grid's pivot table (entries)
+    int z_off;                 // offset of the grid's per-level arrays ((nz+1) entries each)
+    int part_off;              // offset of the grid's partial sums (nz * nrb entries)
+    int twx_off, twy_off;      // offsets of exp(-2 pi i r/N) tables for nx and ny (complex entries)
+    int xblk_off, yzblk_off;   // first block of the grid in x-kernel / yz-kernel launches
+    double dx, dy, rdx, rdy;   // spacings and their inverses
+    double inv_nxy;            // 1 / (nx ny)
+    double sum_hz;             // lz
+};
+
+// Per-level arrays (index z_off + k; nz+1 entries per grid, the last one only used where noted).
+struct ZArrays {
+    double *hz;      // hz_k (k < nz)
+    double *rhz;     // 1/hz_k
+    double *rgzf;    // 1/gz_k on interior faces 1..nz-1, 0 on the wall faces 0 and nz (nz+1 entries)
+    double *az, *cz; // tridiagonal off-diagonals: az_k = rhz_k rgzf_k, cz_k = rhz_k rgzf_{k+1}
+    double *inv00;   // pivots of the pinned (0,0) system (inv00_0 = 0)
+    float *azf, *czf;        // fp32 copies of az, cz
+    float2 *rhz_df, *rgzf_df; // float-float copies (hi, lo) of rhz, rgzf
+};
+
+// Workspace pointers of a plan, passed by value to the kernels.
+struct Work {
+    const GridDev *grids;      // [ngrids]
+    int ngrids;
+    const int *xblk_start;     // prefix of x-kernel blocks over grids [ngrids+1]
+    const int *yzblk_start;    // prefix of yz-kernel blocks over grids [ngrids+1]
+    ZArrays z;
+    void *spec;                // complex<T> spectrum, per grid nz*ncb*ny*mb
+    void *tab;                 // T pivot table, same layout as spec (real entries)
+    const void *twx, *twy;     // complex<T> twiddle tables
+    float2 *bdf;               // float-float right-hand side (mixed path) per cell
+    double *phi_ws;            // per-cell fp64 phi for the adjoint solve
+    double *partial;           // per (grid, k, row block) plane sums of the right-hand side
+    double *partial_phi;       // per (grid, k, row block) plane sums of the current phi (refinement)
+    double *mean_b;            // [ngrids] removed weighted mean of the first right-hand side
+    unsigned long long *maxb;  // [ngrids] max |rhs| (double bits), for max|D u*|
+    unsigned long long *maxdiv;// [ngrids] max |D u| of the output (double bits)
+    unsigned *err;             // device error word (bit i: ibf_status i)
+};
+
+// Per-launch user pointers for up to kGridsPerLaunch grids.
+struct UserPtrs {
+    const double *in_u[kGridsPerLaunch], *in_v[kGridsPerLaunch], *in_w[kGridsPerLaunch], *in_p[kGridsPerLaunch];
+    double *out_u[kGridsPerLaunch], *out_v[kGridsPerLaunch], *out_w[kGridsPerLaunch], *out_p[kGridsPerLaunch];
+    int g0, g1;                // grids [g0, g1) of this launch
+    int blk0;                  // first block index (x-kernel numbering) of grid g0
+};
+
+enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2 };
+enum InvMode { IM_STORE = 0, IM_ACCUM = 1 };
+
+// Launchers (ibf_kernels.cu).  T = 0: fp64 path, 1: mixed path.
+cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int nblk, double s,
+                        double rs, size_t smem, cudaStream_t st);
+cudaError_t launch_yzfwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
+cudaError_t launch_yzbwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
+cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cudaStream_t st);
+cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int nblk, size_t smem,
+                        cudaStream_t st);
+cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int nblk, double s,
+                           cudaStream_t st);
+cudaError_t launch_divstat(int mixed, const Work &w, const UserPtrs &p, int nblk, cudaStream_t st);
+cudaError_t launch_finalize(const Work &w, double *max_div, double *max_div_in, double *compat, double s,
+                            cudaStream_t st);
+cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t st);
+cudaError_t set_smem_limits(int mixed, size_t xsmem, size_t yzsmem);
+
+}  // namespace ibf
