@@ -37,8 +37,8 @@ DT = 1e-3
 SEED = 4
 # Algorithmic HBM bytes per cell of each kernel (fp64 user fields, fp32 spectrum,
 # float-float right-hand side); derivation in the design doc.
-BYTES_MIXED = {"x_forward_div": 36.0, "yz_forward": 10.0, "yz_backward": 10.0, "x_inverse_store": 12.0,
-               "x_forward_residual": 20.0, "x_inverse_accumulate": 20.0, "correct": 56.0, "mode00": 0.0}
+BYTES_MIXED = {"x_forward_div": 36.0, "yz_forward": 10.0, "yz_backward": 10.0, "x_inverse_store": 8.0,
+               "x_forward_residual": 16.0, "x_inverse_accumulate": 16.0, "correct": 64.0, "mode00": 0.0}
 BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x_inverse_store": 16.0,
               "correct": 56.0, "mode00": 0.0}
 

@@ -208,30 +208,47 @@ def _projection_function():
     import torch
 
     class Projection(torch.autograd.Function):
-        """(u*, v*, w*) -> (u, v, w, phi) of a single-grid plan, with ibf_project_backward
-        as its vector-Jacobian product."""
+        """(u*, v*, w*) -> (u, v, w, phi) through a plan, with ibf_project_backward as
+        its vector-Jacobian product.  Unbatched tensors for a one-grid plan, or tensors
+        with a leading batch dimension B for a plan of B grids of identical shape."""
 
         @staticmethod
         def forward(ctx, plan, dt, alpha, u, v, w):
             ctx.plan, ctx.dt, ctx.alpha = plan, dt, alpha
-            uo, vo, wo, po = plan.project(u.contiguous(), v.contiguous(), w.contiguous(), dt, alpha)
+            u, v, w = u.contiguous(), v.contiguous(), w.contiguous()
+            batched = u.dim() == 4
+            ctx.batched = batched
+            n = len(plan.grids)
+            if not batched:
+                uo, vo, wo, po = plan.project(u, v, w, dt, alpha)
+                return uo, vo, wo, po
+            if u.shape[0] != n:
+                raise ValueError("leading dimension must equal the number of grids of the plan")
+            g = plan.grids[0]
+            uo, vo, wo = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
+            po = torch.empty((n, g.nz, g.ny, g.nx), dtype=torch.float64, device=u.device)
+            plan.project_into([(u[b], v[b], w[b]) for b in range(n)],
+                              [(uo[b], vo[b], wo[b], po[b]) for b in range(n)], dt, alpha)
             return uo, vo, wo, po
 
         @staticmethod
         def backward(ctx, gu, gv, gw, gp):
             plan = ctx.plan
+            n = len(plan.grids)
             su, sv, sw = plan.grids[0].shapes
-            dev = None
-            for t in (gu, gv, gw, gp):
-                if t is not None:
-                    dev = t.device
-            z = lambda sh: torch.zeros(sh, dtype=torch.float64, device=dev)
+            pre = (n,) if ctx.batched else ()
+            dev = next(t.device for t in (gu, gv, gw, gp) if t is not None)
+            z = lambda sh: torch.zeros(pre + tuple(sh), dtype=torch.float64, device=dev)
             gu = gu.contiguous() if gu is not None else z(su)
             gv = gv.contiguous() if gv is not None else z(sv)
             gw = gw.contiguous() if gw is not None else z(sw)
             gp = gp.contiguous() if gp is not None else None
             a, b, c = torch.empty_like(gu), torch.empty_like(gv), torch.empty_like(gw)
-            plan.backward_into([(gu, gv, gw, gp)], [(a, b, c)], ctx.dt, ctx.alpha)
+            if ctx.batched:
+                plan.backward_into([(gu[i], gv[i], gw[i], gp[i] if gp is not None else None) for i in range(n)],
+                                   [(a[i], b[i], c[i]) for i in range(n)], ctx.dt, ctx.alpha)
+            else:
+                plan.backward_into([(gu, gv, gw, gp)], [(a, b, c)], ctx.dt, ctx.alpha)
             return None, None, None, a, b, c
 
     return Projection

@@ -154,6 +154,17 @@ ibf_status validate(const ibf_grid *g, std::vector<double> &zf) {
     return IBF_OK;
 }
 
+// magic numbers of FDiv (round-up method, valid for dividends below 2^31)
+FDiv make_fdiv(unsigned d) {
+    FDiv f;
+    f.d = d;
+    unsigned s = 0;
+    while ((1ull << s) < d) ++s;
+    f.s = s;
+    f.m = (unsigned)((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
+    return f;
+}
+
 // exp(-2 pi i r / n), r < n, in fp64 (host libm)
 void twiddles(int n, std::vector<double> &out) {
     out.resize(2 * (size_t)n);
@@ -201,8 +212,11 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
         factor(d.ny, &d.ny1, &d.ny2);
         // y-FFT + tridiagonal column blocks: at most 4096 modes per CTA (shared-memory state),
         // enough blocks overall to fill the GPU twice.
+        // enough modes per block to keep the FFT passes' 64+ tasks busy, but at least one
+        // block per SM over the whole batch
         const int mbmax = std::max(1, std::min(d.nxh, 4096 / d.ny));
-        int mb = (int)std::min<long long>(mbmax, std::max<long long>(1, total_cols / (2 * nsm)));
+        const int want = (64 + d.ny2 - 1) / d.ny2;
+        int mb = (int)std::min<long long>(std::min(mbmax, want), std::max<long long>(1, total_cols / nsm));
         d.mb = mb;
         d.ncb = (d.nxh + mb - 1) / mb;
         // x kernels: rows/2 complex sequences of length nx per CTA, ~64 KB of shared memory
@@ -235,8 +249,21 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
         d.rdx = 1.0 / d.dx; d.rdy = 1.0 / d.dy;
         d.inv_nxy = 1.0 / ((double)d.nx * d.ny);
         d.sum_hz = H.zf[d.nz] - H.zf[0];
+        d.fnx = make_fdiv(d.nx);
+        d.fnx1 = make_fdiv(d.nx1);
+        d.fnx2 = make_fdiv(d.nx2);
+        d.fny1 = make_fdiv(d.ny1);
+        d.fny2 = make_fdiv(d.ny2);
+        d.fmb = make_fdiv(d.mb);
+        d.frows = make_fdiv(d.rows);
+        d.fnpair = make_fdiv(d.rows / 2);
         maxx = std::max(maxx, (size_t)(d.rows / 2) * (size_t)(d.nx1 * (d.nx2 + 1)) * csz);
-        maxyz = std::max(maxyz, (size_t)d.mb * (size_t)(d.ny1 * (d.ny2 + 1) + 1) * csz + (size_t)d.ny * d.mb * csz);
+        {   // yz kernels: kYZStages pipeline stages (see k_yzfwd / k_yzbwd)
+            const size_t sstr = (size_t)(d.ny1 * (d.ny2 + 1) + 1), nslot = (size_t)d.ny * d.mb;
+            const size_t fwd = kYZStages * ((d.mb * sstr * csz + nslot * rsz + 15) & ~(size_t)15) + nslot * csz;
+            const size_t bwd = kYZStages * ((nslot * (csz + rsz) + 15) & ~(size_t)15) + (d.mb * sstr + nslot) * csz;
+            maxyz = std::max(maxyz, std::max(fwd, bwd));
+        }
         pl->maxnz = std::max(pl->maxnz, d.nz);
         pl->total_cells += (long long)d.nx * d.ny * d.nz;
     }
@@ -313,8 +340,13 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
     IBF_TRY(dalloc(pl, &twy, csz * twy_all.size() / 2));
     w.twx = twx;
     w.twy = twy;
-    if (mixed) IBF_TRY(dalloc(pl, &w.bdf, sizeof(float2) * (size_t)cells));
-    IBF_TRY(dalloc(pl, &w.phi_ws, sizeof(double) * (size_t)cells));
+    if (mixed) {
+        IBF_TRY(dalloc(pl, &w.bdf, sizeof(float2) * (size_t)cells));
+        IBF_TRY(dalloc(pl, &w.phi_hi, sizeof(float) * (size_t)cells));
+        IBF_TRY(dalloc(pl, &w.phi_lo, sizeof(float) * (size_t)cells));
+    } else {
+        IBF_TRY(dalloc(pl, &w.phi_ws, sizeof(double) * (size_t)cells));
+    }
     IBF_TRY(dalloc(pl, &w.partial, sizeof(double) * (size_t)std::max(poff, 1)));
     IBF_TRY(dalloc(pl, &w.partial_phi, sizeof(double) * (size_t)std::max(poff, 1)));
     IBF_TRY(dalloc(pl, &w.mean_b, sizeof(double) * ngrids));
@@ -449,31 +481,33 @@ ibf_status run(ibf_plan *pl, const ibf_fields *in, const ibf_fields *out, double
     const Work &w = pl->work;
     const double s = alpha * dt, rs = 1.0 / s;
     const int mixed = pl->mixed;
+    // fp64 path: the adjoint's phi lives in the plan (no phi output); mixed path: phi is
+    // refined as float-float in the plan and written out by the correction kernel.
     const int use_ws = adjoint ? 1 : 0;
+    const int R = mixed ? pl->opts.refine_steps : 0;
     cudaError_t e = cudaMemsetAsync(w.maxb, 0, sizeof(unsigned long long) * pl->ngrids, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.maxdiv, 0, sizeof(unsigned long long) * pl->ngrids, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     const int xmode = adjoint ? XM_ADJ : XM_DIV;
     IBF_TRY(for_chunks(c, adjoint ? "x_forward_adjoint_rhs" : "x_forward_div", in, out, [&](const UserPtrs &p, int nb) {
-        return launch_xfwd(mixed, xmode, w, p, use_ws, nb, s, rs, pl->xsmem, st);
+        return launch_xfwd(mixed, xmode, w, p, use_ws, 0, nb, s, rs, pl->xsmem, st);
     }));
     IBF_TRY(solve_core(c, 1));
     IBF_TRY(for_chunks(c, "x_inverse_store", in, out, [&](const UserPtrs &p, int nb) {
-        return launch_xinv(mixed, IM_STORE, w, p, use_ws, nb, pl->xsmem, st);
+        return launch_xinv(mixed, IM_STORE, w, p, use_ws, 0, nb, pl->xsmem, st);
     }));
-    if (mixed) {
-        for (int r = 0; r < pl->opts.refine_steps; ++r) {
-            IBF_TRY(for_chunks(c, "x_forward_residual", in, out, [&](const UserPtrs &p, int nb) {
-                return launch_xfwd(mixed, XM_RESID, w, p, use_ws, nb, s, rs, pl->xsmem, st);
-            }));
-            IBF_TRY(solve_core(c, 0));
-            IBF_TRY(for_chunks(c, "x_inverse_accumulate", in, out, [&](const UserPtrs &p, int nb) {
-                return launch_xinv(mixed, IM_ACCUM, w, p, use_ws, nb, pl->xsmem, st);
-            }));
-        }
+    for (int r = 0; r < R; ++r) {
+        const int lo_valid = r > 0;
+        IBF_TRY(for_chunks(c, "x_forward_residual", in, out, [&](const UserPtrs &p, int nb) {
+            return launch_xfwd(mixed, XM_RESID, w, p, use_ws, lo_valid, nb, s, rs, pl->xsmem, st);
+        }));
+        IBF_TRY(solve_core(c, 0));
+        IBF_TRY(for_chunks(c, "x_inverse_accumulate", in, out, [&](const UserPtrs &p, int nb) {
+            return launch_xinv(mixed, IM_ACCUM, w, p, use_ws, lo_valid, nb, pl->xsmem, st);
+        }));
     }
     IBF_TRY(for_chunks(c, adjoint ? "correct_adjoint" : "correct", in, out, [&](const UserPtrs &p, int nb) {
-        return launch_correct(mixed, adjoint, w, p, use_ws, nb, s, st);
+        return launch_correct(mixed, adjoint, w, p, use_ws, R > 0, nb, s, st);
     }));
     if (!adjoint && stats && (stats->max_div || stats->max_div_in || stats->compat)) {
         if (stats->max_div) {

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ibf_internal.h"
+
 namespace ibf {
 
 // ------------------------------------------------------------------ complex
@@ -102,31 +104,30 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     return __longlong_as_double((long long)(s | (E << 52) | M));
 }
 
-// df32 -> fp64 without fp64 arithmetic: the two 24-bit significands are
-// aligned in a 64-bit integer and added; the result is truncated to 53 bits.
+// df32 -> fp64 without fp64 arithmetic.  For a normalised pair (|lo| <= ulp(hi),
+// which every df_* operation returns) hi + lo is exactly an fp64 number in hi's
+// binade, so it is hi's fp64 bit pattern plus lo's significand aligned to hi's fp64
+// ulp; the only binade change possible is a borrow below a power of two (hi's
+// fraction zero, lo of opposite sign), where the ulp halves.  lo bits below
+// 2^-52 of hi are truncated.
 __device__ __forceinline__ double df_to_f64(df a) {
     const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
-    const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
-    if (eh == 0) return f32_to_f64(a.lo);          // hi == 0 (or denormal): lo carries the value
-    if (eh == 0xFF) return f32_to_f64(a.hi);       // inf / nan
-    unsigned long long M = (1ull << 52) | ((unsigned long long)(hb & 0x7FFFFFu) << 29);
-    if (el != 0) {
-        const unsigned long long L = (1ull << 23) | (unsigned long long)(lb & 0x7FFFFFu);
-        const int sh = 29 - (eh - el);               // left shift of L into M's units
-        unsigned long long Ls = 0ull;
-        if (sh >= 0) Ls = L << (sh > 40 ? 40 : sh);
-        else if (sh > -40) Ls = L >> (-sh);
-        if ((hb ^ lb) & 0x80000000u) M -= Ls; else M += Ls;
+    const unsigned eh = (hb >> 23) & 0xFFu, el = (lb >> 23) & 0xFFu;
+    if (eh == 0u) return f32_to_f64(a.lo);  // hi zero or subnormal: lo carries the value
+    unsigned long long H = __double_as_longlong(f32_to_f64(a.hi));
+    if (eh == 0xFFu || el == 0u) return __longlong_as_double((long long)H);
+    const unsigned long long L = (unsigned long long)((1u << 23) | (lb & 0x7FFFFFu));
+    const int sh = (int)el - (int)eh + 29;
+    unsigned long long Li = 0ull;
+    if (sh >= 0) Li = L << sh;
+    else if (sh > -25) Li = L >> (-sh);
+    if ((hb ^ lb) & 0x80000000u) {
+        if ((hb & 0x7FFFFFu) == 0u) Li <<= 1;
+        H -= Li;
+    } else {
+        H += Li;
     }
-    int E = eh + 896;
-    if (M >> 53) { M >>= 1; E += 1; }
-    else if (!(M >> 52)) {
-        if (M == 0ull) return __longlong_as_double((long long)((unsigned long long)(hb & 0x80000000u) << 32));
-        const int lz = __clzll((long long)M) - 11;
-        M <<= lz; E -= lz;
-    }
-    return __longlong_as_double((long long)(((unsigned long long)(hb & 0x80000000u) << 32) |
-                                            ((unsigned long long)E << 52) | (M & ((1ull << 52) - 1))));
+    return __longlong_as_double((long long)H);
 }
 
 // ------------------------------------------------------------------ precision policies
@@ -344,42 +345,44 @@ __device__ __forceinline__ void fft_row_task(cx<T> *seq, int q1, int ld, const c
     for (int c = 0; c < P; ++c) row[c] = x[c];
 }
 
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FDiv &f) { return (__umulhi(n, f.m) + n) >> f.s; }
+
 template <typename T, int P, int DIR>
-__device__ __forceinline__ void fft_col_pass_P(cx<T> *buf, int nseq, int sstride, int N2, const cx<T> *tw,
-                                               int tid, int nthr) {
+__device__ __forceinline__ void fft_col_pass_P(cx<T> *buf, int nseq, int sstride, int N2, const FDiv &fN2,
+                                               const cx<T> *tw, int tid, int nthr) {
     const int ntask = nseq * N2;
     for (int t = tid; t < ntask; t += nthr) {
-        const int s = t / N2, c = t - s * N2;
-        fft_col_task<T, P, DIR>(buf + (size_t)s * sstride, c, N2 + 1, tw);
+        const int s = (int)fdiv((unsigned)t, fN2), c = t - s * N2;
+        fft_col_task<T, P, DIR>(buf + s * sstride, c, N2 + 1, tw);
     }
 }
 template <typename T, int P, int DIR>
-__device__ __forceinline__ void fft_row_pass_P(cx<T> *buf, int nseq, int sstride, int N1, int N2, const cx<T> *tw,
-                                               int tid, int nthr) {
+__device__ __forceinline__ void fft_row_pass_P(cx<T> *buf, int nseq, int sstride, int N1, int N2, const FDiv &fN1,
+                                               const cx<T> *tw, int tid, int nthr) {
     const int ntask = nseq * N1;
     for (int t = tid; t < ntask; t += nthr) {
-        const int s = t / N1, q1 = t - s * N1;
-        fft_row_task<T, P, DIR>(buf + (size_t)s * sstride, q1, N2 + 1, tw);
+        const int s = (int)fdiv((unsigned)t, fN1), q1 = t - s * N1;
+        fft_row_task<T, P, DIR>(buf + s * sstride, q1, N2 + 1, tw);
     }
 }
 
 #define IBF_FFT_SIZES(X) X(1) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32)
 
 template <typename T, int DIR>
-__device__ __forceinline__ void fft_col_pass(cx<T> *buf, int nseq, int sstride, int N1, int N2, const cx<T> *tw,
-                                          int tid, int nthr) {
+__device__ __forceinline__ void fft_col_pass(cx<T> *buf, int nseq, int sstride, int N1, int N2, const FDiv &fN2,
+                                             const cx<T> *tw, int tid, int nthr) {
     switch (N1) {
-#define IBF_CASE(P) case P: fft_col_pass_P<T, P, DIR>(buf, nseq, sstride, N2, tw, tid, nthr); break;
+#define IBF_CASE(P) case P: fft_col_pass_P<T, P, DIR>(buf, nseq, sstride, N2, fN2, tw, tid, nthr); break;
         IBF_FFT_SIZES(IBF_CASE)
 #undef IBF_CASE
         default: break;
     }
 }
 template <typename T, int DIR>
-__device__ __forceinline__ void fft_row_pass(cx<T> *buf, int nseq, int sstride, int N1, int N2, const cx<T> *tw,
-                                          int tid, int nthr) {
+__device__ __forceinline__ void fft_row_pass(cx<T> *buf, int nseq, int sstride, int N1, int N2, const FDiv &fN1,
+                                             const cx<T> *tw, int tid, int nthr) {
     switch (N2) {
-#define IBF_CASE(P) case P: fft_row_pass_P<T, P, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr); break;
+#define IBF_CASE(P) case P: fft_row_pass_P<T, P, DIR>(buf, nseq, sstride, N1, N2, fN1, tw, tid, nthr); break;
         IBF_FFT_SIZES(IBF_CASE)
 #undef IBF_CASE
         default: break;
@@ -388,18 +391,27 @@ __device__ __forceinline__ void fft_row_pass(cx<T> *buf, int nseq, int sstride, 
 
 // Batch of nseq sequences at buf + s * sstride.  Ends with a __syncthreads().
 template <typename T, int DIR>
-__device__ __forceinline__ void fft_batch(cx<T> *buf, int nseq, int sstride, int N1, int N2, const cx<T> *tw) {
+__device__ __forceinline__ void fft_batch(cx<T> *buf, int nseq, int sstride, int N1, int N2, const FDiv &fN1,
+                                          const FDiv &fN2, const cx<T> *tw) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (DIR < 0) {
-        fft_col_pass<T, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr);
+        fft_col_pass<T, DIR>(buf, nseq, sstride, N1, N2, fN2, tw, tid, nthr);
         __syncthreads();
-        fft_row_pass<T, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr);
+        fft_row_pass<T, DIR>(buf, nseq, sstride, N1, N2, fN1, tw, tid, nthr);
     } else {
-        fft_row_pass<T, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr);
+        fft_row_pass<T, DIR>(buf, nseq, sstride, N1, N2, fN1, tw, tid, nthr);
         __syncthreads();
-        fft_col_pass<T, DIR>(buf, nseq, sstride, N1, N2, tw, tid, nthr);
+        fft_col_pass<T, DIR>(buf, nseq, sstride, N1, N2, fN2, tw, tid, nthr);
     }
     __syncthreads();
+}
+
+// natural position p -> (p / N2) (N2+1) + p % N2 = p + p / N2
+__device__ __forceinline__ int pos_nat(int p, const FDiv &fN2) { return p + (int)fdiv((unsigned)p, fN2); }
+// transposed position of mode q: (q % N1) (N2+1) + q / N1
+__device__ __forceinline__ int pos_tr(int q, int N1, int N2, const FDiv &fN1) {
+    const int a = (int)fdiv((unsigned)q, fN1);
+    return (q - a * N1) * (N2 + 1) + a;
 }
 
 }  // namespace ibf

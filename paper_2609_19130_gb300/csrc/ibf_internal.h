@@ -11,6 +11,13 @@ constexpr int kGridsPerLaunch = 32;
 // Thread counts of the kernels.
 constexpr int kXThreads = 256;   // x-direction (row) kernels and stencil kernels
 constexpr int kYZThreads = 128;  // y-FFT + z-tridiagonal column kernels
+constexpr int kYZStages = 2;     // planes in flight per column block in the yz kernels
+
+// Division by a run-time invariant d (Granlund & Montgomery, PLDI 1994, round-up
+// variant): n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31.
+struct FDiv {
+    unsigned d, m, s;
+};
 
 // Per-grid descriptor, one entry per grid in device memory.
 struct GridDev {
@@ -28,6 +35,7 @@ struct GridDev {
     double dx, dy, rdx, rdy;   // spacings and their inverses
     double inv_nxy;            // 1 / (nx ny)
     double sum_hz;             // lz
+    FDiv fnx, fnx1, fnx2, fny1, fny2, fmb, frows, fnpair;
 };
 
 // Per-level arrays (index z_off + k; nz+1 entries per grid, the last one only used where noted).
@@ -52,7 +60,8 @@ struct Work {
     void *tab;                 // T pivot table, same layout as spec (real entries)
     const void *twx, *twy;     // complex<T> twiddle tables
     float2 *bdf;               // float-float right-hand side (mixed path) per cell
-    double *phi_ws;            // per-cell fp64 phi for the adjoint solve
+    double *phi_ws;            // per-cell fp64 phi of the adjoint solve (fp64 path)
+    float *phi_hi, *phi_lo;    // per-cell float-float phi being refined (mixed path)
     double *partial;           // per (grid, k, row block) plane sums of the right-hand side
     double *partial_phi;       // per (grid, k, row block) plane sums of the current phi (refinement)
     double *mean_b;            // [ngrids] removed weighted mean of the first right-hand side
@@ -73,15 +82,15 @@ enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2 };
 enum InvMode { IM_STORE = 0, IM_ACCUM = 1 };
 
 // Launchers (ibf_kernels.cu).  T = 0: fp64 path, 1: mixed path.
-cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int nblk, double s,
-                        double rs, size_t smem, cudaStream_t st);
+cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
+                        double s, double rs, size_t smem, cudaStream_t st);
 cudaError_t launch_yzfwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_yzbwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cudaStream_t st);
-cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int nblk, size_t smem,
-                        cudaStream_t st);
-cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int nblk, double s,
-                           cudaStream_t st);
+cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
+                        size_t smem, cudaStream_t st);
+cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
+                           int nblk, double s, cudaStream_t st);
 cudaError_t launch_divstat(int mixed, const Work &w, const UserPtrs &p, int nblk, cudaStream_t st);
 cudaError_t launch_finalize(const Work &w, double *max_div, double *max_div_in, double *compat, double s,
                             cudaStream_t st);

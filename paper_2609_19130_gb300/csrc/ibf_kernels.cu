@@ -38,6 +38,9 @@ __device__ __forceinline__ int find_grid(const int *start, int n, int b) {
     return lo;
 }
 
+template <class A> struct IsDF { static constexpr bool value = false; };
+template <> struct IsDF<DFArith> { static constexpr bool value = true; };
+
 template <class A> struct Coef;
 template <> struct Coef<F64Arith> {
     __device__ __forceinline__ static double c(double x) { return x; }
@@ -106,9 +109,69 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double 
     atomicMax(p, (unsigned long long)__double_as_longlong(v));
 }
 
+// ---------------------------------------------------------------- warp helpers
+template <class V> __device__ __forceinline__ V shdown(V v, int d);
+template <> __device__ __forceinline__ df shdown<df>(df v, int d) {
+    return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+template <> __device__ __forceinline__ double shdown<double>(double v, int d) {
+    return __shfl_down_sync(0xffffffffu, v, d);
+}
+template <class V> __device__ __forceinline__ V shup(V v, int d);
+template <> __device__ __forceinline__ df shup<df>(df v, int d) {
+    return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+template <> __device__ __forceinline__ double shup<double>(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+
+// phi of the solve being refined: float-float (hi, lo) arrays on the mixed path
+// (lo absent before the first accumulation), fp64 array on the fp64 path.
+template <class A> struct PhiSrc;
+template <> struct PhiSrc<DFArith> {
+    const float *hi, *lo;
+    __device__ __forceinline__ df get(ptrdiff_t o) const { return {__ldg(hi + o), lo ? __ldg(lo + o) : 0.f}; }
+};
+template <> struct PhiSrc<F64Arith> {
+    const double *p;
+    __device__ __forceinline__ double get(ptrdiff_t o) const { return __ldg(p + o); }
+};
+
+// Cells of a CTA's (plane, rows) block are visited by warps in 32-wide row
+// segments: lanes hold consecutive i (x-neighbours by shuffle), and each warp
+// walks its rows upward (y-neighbours carried in registers).  With fewer segments
+// than warps the rows are split into chunks.
+struct SegMap {
+    int seg0, segstep, nseg, r0, r1;
+};
+__device__ __forceinline__ SegMap seg_map(int nx, int rows) {
+    const int warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    SegMap m;
+    m.nseg = (nx + 31) >> 5;
+    if (m.nseg >= NW) {
+        m.seg0 = warp; m.segstep = NW; m.r0 = 0; m.r1 = rows;
+    } else {
+        const int nchunk = NW / m.nseg;
+        const int chunk = warp / m.nseg;
+        m.seg0 = warp - chunk * m.nseg;
+        m.segstep = m.nseg;
+        if (chunk >= nchunk) {
+            m.seg0 = m.nseg; m.r0 = 0; m.r1 = 0;
+        } else {
+            const int rpc = (rows + nchunk - 1) / nchunk;
+            m.r0 = min(rows, chunk * rpc);
+            m.r1 = min(rows, m.r0 + rpc);
+        }
+    }
+    return m;
+}
+
 // ================================================================ k_xfwd
+constexpr int kRowGroup = 4;  // rows whose loads are issued together (memory-level parallelism)
+
+// Right-hand side of one solve for a block of rows of plane k, then the real FFT
+// along x of the rows (two rows per complex transform), stored as x-modes.
 template <typename T, class A, int MODE>
-__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1) k_xfwd(Work w, UserPtrs p, int use_ws, double s, double rs) {
+__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
+    k_xfwd(Work w, UserPtrs p, int use_ws, int lo_valid, double s, double rs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
     __shared__ double red[kXThreads / 32];
@@ -124,11 +187,12 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1) k_xfwd(Work
     const int j0 = rb * rows;
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     const int N1 = G.nx1, N2 = G.nx2, sstride = fft_seq_len(N1, N2);
+    const FDiv fN1 = G.fnx1, fN2 = G.fnx2;
     const int gi = g - p.g0;
     const int zo = G.z_off;
-    const size_t plane = (size_t)nx * ny;
+    const ptrdiff_t plane = (ptrdiff_t)nx * ny;
+    const ptrdiff_t pbase = (ptrdiff_t)k * plane;
 
-    // per-CTA coefficients
     V cu, cv, cwp, cwm, cp;
     if (MODE == XM_DIV) {
         const double rhz = w.z.rhz[zo + k];
@@ -144,7 +208,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1) k_xfwd(Work
         cwp = Coef<A>::c(rhz * w.z.rgzf[zo + k + 1]);
         cwm = Coef<A>::c(rhz * w.z.rgzf[zo + k]);
         cp = Coef<A>::c(rs * rhz);
-    } else {  // residual: b - <b> - L phi,  L phi = rdx^2 d2x + rdy^2 d2y + rhz (rgzf+ dz+ - rgzf- dz-)
+    } else {  // residual b - <b> - L phi, L phi = rdx^2 d2x + rdy^2 d2y + rhz (rgzf+ dz+ - rgzf- dz-)
         cu = Coef<A>::c(G.rdx * G.rdx);
         cv = Coef<A>::c(G.rdy * G.rdy);
         const double rhz = w.z.rhz[zo + k];
@@ -155,60 +219,156 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1) k_xfwd(Work
     const T scale = (T)G.inv_nxy;
 
     V acc = A::zero();
-    V acc_phi = A::zero();  // residual mode: plane sum of the current phi (for its weighted mean)
+    V acc_phi = A::zero();  // residual mode: plane sum of the current phi
     float vmax = 0.f;
-    const int ncell = rows * nx;
-    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-        const int jl = t / nx, i = t - jl * nx;
-        const int j = j0 + jl;
-        T val = (T)0;
-        if (j < ny) {
-            const int ip = (i + 1 == nx) ? 0 : i + 1;
-            const int jp = (j + 1 == ny) ? 0 : j + 1;
-            const size_t c = (size_t)k * plane + (size_t)j * nx + i;
-            V bv;
-            if (MODE == XM_DIV || MODE == XM_ADJ) {
-                const double *u = p.in_u[gi], *vv = p.in_v[gi], *ww = p.in_w[gi];
-                const size_t rowk = (size_t)k * plane + (size_t)j * nx;
-                V du = A::sub(A::load(__ldg(u + rowk + ip)), A::load(__ldg(u + rowk + i)));
-                V dv = A::sub(A::load(__ldg(vv + (size_t)k * plane + (size_t)jp * nx + i)), A::load(__ldg(vv + c)));
-                V w1 = A::load(__ldg(ww + c + plane)), w0 = A::load(__ldg(ww + c));
-                bv = A::add(A::mul(cu, du), A::mul(cv, dv));
-                if (MODE == XM_DIV) bv = A::add(bv, A::mul(cwp, A::sub(w1, w0)));
-                else {
-                    bv = A::add(bv, A::sub(A::mul(cwp, w1), A::mul(cwm, w0)));
-                    if (p.in_p[gi]) bv = A::add(bv, A::mul(cp, A::load(__ldg(p.in_p[gi] + c))));
+    const int lane = threadIdx.x & 31;
+    const SegMap sm = seg_map(nx, rows);
+    for (int seg = sm.seg0; seg < sm.nseg; seg += sm.segstep) {
+        const int i = seg * 32 + lane;
+        const bool act = i < nx;
+        const int ii = act ? i : nx - 1;  // inactive lanes load a valid cell and discard it
+        const int ip = (ii + 1 == nx) ? 0 : ii + 1;
+        const int im = (ii == 0) ? nx - 1 : ii - 1;
+        const bool own_up = (lane == 31) || (ii + 1 == nx);
+        const bool own_dn = (lane == 0) || (ii == 0);
+        const int spos = pos_nat(ii, fN2);
+        if (MODE == XM_DIV || MODE == XM_ADJ) {
+            const double *u = p.in_u[gi] + pbase, *vv = p.in_v[gi] + pbase, *ww = p.in_w[gi] + pbase;
+            const double *pp = (MODE == XM_ADJ && p.in_p[gi]) ? p.in_p[gi] + pbase : nullptr;
+            V vcur = A::zero();
+            bool have_v = false;
+            for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
+                // load phase: every fp64 input of up to kRowGroup rows is requested first
+                double ru[kRowGroup], rue[kRowGroup], rvn[kRowGroup], rw0[kRowGroup], rw1[kRowGroup],
+                    rp[kRowGroup];
+                double rv0 = 0.0;
+                const bool need_v0 = !have_v;
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+                    ru[q] = rue[q] = rvn[q] = rw0[q] = rw1[q] = rp[q] = 0.0;
+                    if (jl < sm.r1 && j < ny) {
+                        const int jp = (j + 1 == ny) ? 0 : j + 1;
+                        const int row = j * nx;
+                        ru[q] = __ldg(u + row + ii);
+                        if (own_up) rue[q] = __ldg(u + row + ip);
+                        if (q == 0 && need_v0) rv0 = __ldg(vv + row + ii);
+                        rvn[q] = __ldg(vv + jp * nx + ii);
+                        rw0[q] = __ldg(ww + row + ii);
+                        rw1[q] = __ldg(ww + plane + row + ii);
+                        if (MODE == XM_ADJ && pp) rp[q] = __ldg(pp + row + ii);
+                    }
                 }
-                if (MODE == XM_DIV) vmax = fmaxf(vmax, absv<A>(bv));
-                if (sizeof(T) == 4) w.bdf[G.cell_off + c] = *reinterpret_cast<const float2 *>(&bv);
-            } else {
-                const double *ph = use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi];
-                const int im = (i == 0) ? nx - 1 : i - 1;
-                const int jm = (j == 0) ? ny - 1 : j - 1;
-                const size_t rowk = (size_t)k * plane + (size_t)j * nx;
-                const V pc = A::load(__ldg(ph + c));
-                acc_phi = A::add(acc_phi, pc);
-                const V dxp = A::sub(A::load(__ldg(ph + rowk + ip)), pc);
-                const V dxm = A::sub(pc, A::load(__ldg(ph + rowk + im)));
-                const V dyp = A::sub(A::load(__ldg(ph + (size_t)k * plane + (size_t)jp * nx + i)), pc);
-                const V dym = A::sub(pc, A::load(__ldg(ph + (size_t)k * plane + (size_t)jm * nx + i)));
-                const V dzp = (k + 1 < nz) ? A::sub(A::load(__ldg(ph + c + plane)), pc) : A::zero();
-                const V dzm = (k > 0) ? A::sub(pc, A::load(__ldg(ph + c - plane))) : A::zero();
-                V lap = A::add(A::mul(cu, A::sub(dxp, dxm)), A::mul(cv, A::sub(dyp, dym)));
-                lap = A::add(lap, A::sub(A::mul(cwp, dzp), A::mul(cwm, dzm)));
-                const float2 bb = w.bdf[G.cell_off + c];
-                V bvv;
-                if (sizeof(T) == 4) bvv = *reinterpret_cast<const V *>(&bb);
-                else bvv = A::zero();
-                bv = A::sub(A::sub(bvv, cp), lap);
+                if (need_v0) vcur = A::load(rv0);
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+                    if (jl >= sm.r1) break;  // warp-uniform
+                    T val = (T)0;
+                    if (j < ny) {
+                        const int row = j * nx;
+                        const V U = A::load(ru[q]);
+                        V Un = shdown(U, 1);
+                        if (own_up) Un = A::load(rue[q]);
+                        const V Vn = A::load(rvn[q]);
+                        const V W0 = A::load(rw0[q]), W1 = A::load(rw1[q]);
+                        V bv = A::add(A::mul(cu, A::sub(Un, U)), A::mul(cv, A::sub(Vn, vcur)));
+                        if (MODE == XM_DIV) {
+                            bv = A::add(bv, A::mul(cwp, A::sub(W1, W0)));
+                        } else {
+                            bv = A::add(bv, A::sub(A::mul(cwp, W1), A::mul(cwm, W0)));
+                            if (pp) bv = A::add(bv, A::mul(cp, A::load(rp[q])));
+                        }
+                        vcur = Vn;
+                        have_v = true;
+                        if (act) {
+                            if (MODE == XM_DIV) vmax = fmaxf(vmax, absv<A>(bv));
+                            if (sizeof(T) == 4)
+                                w.bdf[G.cell_off + pbase + row + i] = *reinterpret_cast<const float2 *>(&bv);
+                            acc = A::add(acc, bv);
+                            val = to_T<T, A>(bv) * scale;
+                        }
+                    } else {
+                        have_v = false;
+                    }
+                    if (act) *(reinterpret_cast<T *>(buf + (jl >> 1) * sstride + spos) + (jl & 1)) = val;
+                }
             }
-            acc = A::add(acc, bv);
-            val = to_T<T, A>(bv) * scale;
+        } else {
+            PhiSrc<A> ph;
+            if constexpr (sizeof(T) == 4) {
+                ph.hi = w.phi_hi + G.cell_off + pbase;
+                ph.lo = lo_valid ? w.phi_lo + G.cell_off + pbase : nullptr;
+            }
+            const float2 *bd = w.bdf + G.cell_off + pbase;
+            V Pm = A::zero(), Pc = A::zero();
+            bool have = false;
+            for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
+                V pn[kRowGroup], pkp[kRowGroup], pkm[kRowGroup], peu[kRowGroup], ped[kRowGroup];
+                float2 bdv[kRowGroup];
+                V pm0 = A::zero(), pc0 = A::zero();
+                const bool need0 = !have;
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+                    pn[q] = pkp[q] = pkm[q] = peu[q] = ped[q] = A::zero();
+                    bdv[q] = make_float2(0.f, 0.f);
+                    if (jl < sm.r1 && j < ny) {
+                        const int jp = (j + 1 == ny) ? 0 : j + 1;
+                        const int jm = (j == 0) ? ny - 1 : j - 1;
+                        const int row = j * nx;
+                        if (q == 0 && need0) {
+                            pm0 = ph.get(jm * nx + ii);
+                            pc0 = ph.get(row + ii);
+                        }
+                        pn[q] = ph.get(jp * nx + ii);
+                        if (k + 1 < nz) pkp[q] = ph.get(plane + row + ii);
+                        if (k > 0) pkm[q] = ph.get(row + ii - plane);
+                        if (own_up) peu[q] = ph.get(row + ip);
+                        if (own_dn) ped[q] = ph.get(row + im);
+                        if (act) bdv[q] = __ldg(bd + row + i);
+                    }
+                }
+                if (need0) {
+                    Pm = pm0;
+                    Pc = pc0;
+                }
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+                    if (jl >= sm.r1) break;
+                    T val = (T)0;
+                    if (j < ny) {
+                        V Pip = shdown(Pc, 1);
+                        if (own_up) Pip = peu[q];
+                        V Pim = shup(Pc, 1);
+                        if (own_dn) Pim = ped[q];
+                        const V dzp = (k + 1 < nz) ? A::sub(pkp[q], Pc) : A::zero();
+                        const V dzm = (k > 0) ? A::sub(Pc, pkm[q]) : A::zero();
+                        const V dxp = A::sub(Pip, Pc), dxm = A::sub(Pc, Pim);
+                        const V dyp = A::sub(pn[q], Pc), dym = A::sub(Pc, Pm);
+                        V lap = A::add(A::mul(cu, A::sub(dxp, dxm)), A::mul(cv, A::sub(dyp, dym)));
+                        lap = A::add(lap, A::sub(A::mul(cwp, dzp), A::mul(cwm, dzm)));
+                        if (act) {
+                            V bvv = A::zero();
+                            if constexpr (sizeof(T) == 4) bvv = df{bdv[q].x, bdv[q].y};
+                            const V bv = A::sub(A::sub(bvv, cp), lap);
+                            acc = A::add(acc, bv);
+                            acc_phi = A::add(acc_phi, Pc);
+                            val = to_T<T, A>(bv) * scale;
+                        }
+                        Pm = Pc;
+                        Pc = pn[q];
+                        have = true;
+                    } else {
+                        have = false;
+                    }
+                    if (act) *(reinterpret_cast<T *>(buf + (jl >> 1) * sstride + spos) + (jl & 1)) = val;
+                }
+            }
         }
-        T *slot = reinterpret_cast<T *>(buf + (size_t)(jl >> 1) * sstride + fft_pos_nat(i, N2)) + (jl & 1);
-        *slot = val;
     }
-    // plane sum of this block's rows (for the singular mode), fixed reduction order
+    // plane sums of this block's rows (for the singular mode), fixed reduction order
     V tot = Red<A>::sum(acc, red);
     if (threadIdx.x == 0) w.partial[G.part_off + k * nrb + rb] = A::store(tot);
     if (MODE == XM_RESID) {
@@ -222,21 +382,23 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1) k_xfwd(Work
     __syncthreads();
 
     const cx<T> *twx = reinterpret_cast<const cx<T> *>(w.twx) + G.twx_off;
-    fft_batch<T, -1>(buf, rows >> 1, sstride, N1, N2, twx);
+    fft_batch<T, -1>(buf, rows >> 1, sstride, N1, N2, fN1, fN2, twx);
 
     // split the two real rows and store x-modes m = 0..nx/2 in column blocks
     const int mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + (size_t)k * ncb * ny * mb;
     const int nout = ncb * rows * mb;
+    const FDiv fmb = G.fmb, frows = G.frows;
     for (int t = threadIdx.x; t < nout; t += blockDim.x) {
-        const int mm = t % mb;
-        const int rest = t / mb;
-        const int jl = rest % rows, cb = rest / rows;
+        const int rest = (int)fdiv((unsigned)t, fmb);
+        const int mm = t - rest * mb;
+        const int cb = (int)fdiv((unsigned)rest, frows);
+        const int jl = rest - cb * rows;
         const int m = cb * mb + mm, j = j0 + jl;
         if (m >= nxh || j >= ny) continue;
-        const cx<T> *seq = buf + (size_t)(jl >> 1) * sstride;
-        const cx<T> Zm = seq[fft_pos_tr(m, N1, N2)];
-        const cx<T> Zc = seq[fft_pos_tr(m == 0 ? 0 : nx - m, N1, N2)];
+        const cx<T> *seq = buf + (jl >> 1) * sstride;
+        const cx<T> Zm = seq[pos_tr(m, N1, N2, fN1)];
+        const cx<T> Zc = seq[pos_tr(m == 0 ? 0 : nx - m, N1, N2, fN1)];
         cx<T> X;
         if ((jl & 1) == 0) X = {(Zm.x + Zc.x) * (T)0.5, (Zm.y - Zc.y) * (T)0.5};
         else X = {(Zm.y + Zc.y) * (T)0.5, (Zc.x - Zm.x) * (T)0.5};
@@ -249,90 +411,162 @@ template <typename T> __device__ __forceinline__ const T *zarr(const double *d, 
 template <> __device__ __forceinline__ const double *zarr<double>(const double *d, const float *) { return d; }
 template <> __device__ __forceinline__ const float *zarr<float>(const double *, const float *f) { return f; }
 
+// cp.async (sm_80+ asynchronous global->shared copy, L1-bypassing for 16 B) of one element
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem_src), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// y-FFT + Thomas forward elimination of one column block, sweeping k = 0..nz-1.
+// Shared memory: kYZStages x [FFT buffer (mb padded sequences) | pivot chunk], then the
+// Thomas state d'_{k-1} of every mode of the block.  Plane k+1 (spectrum and pivots)
+// is copied with cp.async while plane k is transformed and eliminated.
 template <typename T>
-__global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? 4 : 2) k_yzfwd(Work w) {
+__global__ void __launch_bounds__(kYZThreads) k_yzfwd(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
     const int g = find_grid(w.yzblk_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
     const int cb = blockIdx.x - __ldg(w.yzblk_start + g);
     const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
     const int nslot = ny * mb;
+    const int nvalid = min(mb, nxh - cb * mb);  // valid x-modes of this block
     const cx<T> *twy = reinterpret_cast<const cx<T> *>(w.twy) + G.twy_off;
     const T *az = zarr<T>(w.z.az, w.z.azf) + G.z_off;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    const size_t fftsz = (size_t)mb * sstride;  // complex elements of one FFT buffer
+    const size_t stage_bytes = ((fftsz * sizeof(cx<T>) + (size_t)nslot * sizeof(T)) + 15) & ~(size_t)15;
+    auto fbuf = [&](int st) { return reinterpret_cast<cx<T> *>(smem_raw + st * stage_bytes); };
+    auto tbuf = [&](int st) { return reinterpret_cast<T *>(smem_raw + st * stage_bytes + fftsz * sizeof(cx<T>)); };
+    cx<T> *state = reinterpret_cast<cx<T> *>(smem_raw + kYZStages * stage_bytes);
+    const cx<T> *spec = reinterpret_cast<const cx<T> *>(w.spec) + G.spec_off;
+    cx<T> *specw = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
+    const T *tab = reinterpret_cast<const T *>(w.tab) + G.tab_off;
 
-    // Thomas state d'_{k-1} of every mode of the block, in shared memory after the FFT buffer
-    cx<T> *state = buf + (size_t)mb * sstride;
+    auto issue = [&](int k) {
+        if (k < nz) {
+            const int st = k % kYZStages;
+            cx<T> *fb = fbuf(st);
+            T *tb = tbuf(st);
+            const cx<T> *src = spec + ((size_t)k * ncb + cb) * nslot;
+            const T *tsrc = tab + ((size_t)k * ncb + cb) * nslot;
+            for (int t = tid; t < nslot; t += nthr) {
+                const int j = (int)fdiv((unsigned)t, fmb), mm = t - j * mb;
+                cx<T> *dst = fb + mm * sstride + pos_nat(j, fN2);
+                if (mm < nvalid) cp_async<sizeof(cx<T>)>(dst, src + t);
+                else *dst = {(T)0, (T)0};
+                cp_async<sizeof(T)>(tb + t, tsrc + t);
+            }
+        }
+        cp_async_commit();
+    };
+
     for (int q = tid; q < nslot; q += nthr) state[q] = {(T)0, (T)0};
+    for (int k = 0; k < kYZStages - 1; ++k) issue(k);
 
     for (int k = 0; k < nz; ++k) {
-        cx<T> *pl = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + ((size_t)k * ncb + cb) * nslot;
-        const T *tabk = reinterpret_cast<const T *>(w.tab) + G.tab_off + ((size_t)k * ncb + cb) * nslot;
-        for (int t = tid; t < nslot; t += nthr) {
-            const int mm = t % mb, j = t / mb;
-            cx<T> v = {(T)0, (T)0};
-            if (cb * mb + mm < nxh) v = pl[t];
-            buf[mm * sstride + fft_pos_nat(j, N2)] = v;
-        }
+        issue(k + kYZStages - 1);
+        cp_async_wait<kYZStages - 1>();
         __syncthreads();
-        fft_batch<T, -1>(buf, mb, sstride, N1, N2, twy);
+        cx<T> *buf = fbuf(k % kYZStages);
+        const T *tb = tbuf(k % kYZStages);
+        fft_batch<T, -1>(buf, mb, sstride, N1, N2, fN1, fN2, twy);
+        cx<T> *pl = specw + ((size_t)k * ncb + cb) * nslot;
         const T a = az[k];
         for (int q = tid; q < nslot; q += nthr) {
-            const int mm = q % mb, sn = q / mb;
-            const cx<T> rin = buf[mm * sstride + (sn / N2) * (N2 + 1) + (sn % N2)];
-            const T inv = __ldg(tabk + q);
+            const int sn = (int)fdiv((unsigned)q, fmb), mm = q - sn * mb;
+            const cx<T> rin = buf[mm * sstride + pos_nat(sn, fN2)];
+            const T inv = tb[q];
             const cx<T> dp = state[q];
             cx<T> d = {(rin.x - a * dp.x) * inv, (rin.y - a * dp.y) * inv};
             if (cb == 0 && q == 0) d = rin;  // (0,0) mode: solved by k_00
             state[q] = d;
-            if (cb * mb + mm < nxh) pl[q] = d;
+            if (mm < nvalid) pl[q] = d;
         }
         __syncthreads();
     }
+    cp_async_wait<0>();
 }
 
+// Back substitution and inverse y-FFT of one column block, sweeping k = nz-1..0.
+// Shared memory: kYZStages x [d' chunk (slot order) | pivot chunk], then one FFT
+// buffer and the state phi_hat_{k+1}; plane k-1 is copied while plane k is processed.
 template <typename T>
-__global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? 4 : 2) k_yzbwd(Work w) {
+__global__ void __launch_bounds__(kYZThreads) k_yzbwd(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
     const int g = find_grid(w.yzblk_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
     const int cb = blockIdx.x - __ldg(w.yzblk_start + g);
     const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
     const int nslot = ny * mb;
+    const int nvalid = min(mb, nxh - cb * mb);
     const cx<T> *twy = reinterpret_cast<const cx<T> *>(w.twy) + G.twy_off;
     const T *cz = zarr<T>(w.z.cz, w.z.czf) + G.z_off;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    const size_t stage_bytes = (((size_t)nslot * (sizeof(cx<T>) + sizeof(T))) + 15) & ~(size_t)15;
+    auto dbuf = [&](int st) { return reinterpret_cast<cx<T> *>(smem_raw + st * stage_bytes); };
+    auto tbuf = [&](int st) { return reinterpret_cast<T *>(smem_raw + st * stage_bytes + (size_t)nslot * sizeof(cx<T>)); };
+    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw + kYZStages * stage_bytes);
+    cx<T> *state = buf + (size_t)mb * sstride;
+    cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
+    const T *tab = reinterpret_cast<const T *>(w.tab) + G.tab_off;
 
-    cx<T> *state = buf + (size_t)mb * sstride;  // phi_hat_{k+1} of every mode of the block
+    auto issue = [&](int k) {  // plane k (k >= 0) into stage (nz-1-k) % S
+        if (k >= 0) {
+            const int st = (nz - 1 - k) % kYZStages;
+            cx<T> *db = dbuf(st);
+            T *tb = tbuf(st);
+            const cx<T> *src = spec + ((size_t)k * ncb + cb) * nslot;
+            const T *tsrc = tab + ((size_t)k * ncb + cb) * nslot;
+            for (int t = tid; t < nslot; t += nthr) {
+                const int sn = (int)fdiv((unsigned)t, fmb), mm = t - sn * mb;
+                if (mm < nvalid) cp_async<sizeof(cx<T>)>(db + t, src + t);
+                else db[t] = {(T)0, (T)0};
+                cp_async<sizeof(T)>(tb + t, tsrc + t);
+            }
+        }
+        cp_async_commit();
+    };
+
     for (int q = tid; q < nslot; q += nthr) state[q] = {(T)0, (T)0};
+    for (int s_ = 0; s_ < kYZStages - 1; ++s_) issue(nz - 1 - s_);
 
     for (int k = nz - 1; k >= 0; --k) {
-        cx<T> *pl = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + ((size_t)k * ncb + cb) * nslot;
-        const T *tabk = reinterpret_cast<const T *>(w.tab) + G.tab_off + ((size_t)k * ncb + cb) * nslot;
+        issue(k - (kYZStages - 1));
+        cp_async_wait<kYZStages - 1>();
+        __syncthreads();
+        const int st = (nz - 1 - k) % kYZStages;
+        const cx<T> *db = dbuf(st);
+        const T *tb = tbuf(st);
         const T c = cz[k];
         for (int q = tid; q < nslot; q += nthr) {
-            const int mm = q % mb, sn = q / mb;
-            cx<T> d = {(T)0, (T)0};
-            if (cb * mb + mm < nxh) d = pl[q];
-            const T cp = c * __ldg(tabk + q);
+            const int sn = (int)fdiv((unsigned)q, fmb), mm = q - sn * mb;
+            const cx<T> d = db[q];
+            const T cp = c * tb[q];
             const cx<T> nx_ = state[q];
             cx<T> ph = {d.x - cp * nx_.x, d.y - cp * nx_.y};
             if (cb == 0 && q == 0) ph = d;
             state[q] = ph;
-            buf[mm * sstride + (sn / N2) * (N2 + 1) + (sn % N2)] = ph;
+            buf[mm * sstride + pos_nat(sn, fN2)] = ph;
         }
         __syncthreads();
-        fft_batch<T, +1>(buf, mb, sstride, N1, N2, twy);
+        fft_batch<T, +1>(buf, mb, sstride, N1, N2, fN1, fN2, twy);
+        cx<T> *pl = spec + ((size_t)k * ncb + cb) * nslot;
         for (int t = tid; t < nslot; t += nthr) {
-            const int mm = t % mb, j = t / mb;
-            if (cb * mb + mm < nxh) pl[t] = buf[mm * sstride + fft_pos_nat(j, N2)];
+            const int j = (int)fdiv((unsigned)t, fmb), mm = t - j * mb;
+            if (mm < nvalid) pl[t] = buf[mm * sstride + pos_nat(j, fN2)];
         }
         __syncthreads();
     }
+    cp_async_wait<0>();
 }
 
 // ================================================================ k_00 (fp64, one CTA per grid)
@@ -395,8 +629,12 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
 }
 
 // ================================================================ k_xinv
+// Inverse real FFT along x of a block of rows; STORE writes phi (fp64 path: fp64
+// array; mixed path: the hi array of the float-float phi), ACCUM adds the
+// refinement correction to the float-float phi.
 template <typename T, class A, int IMODE>
-__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1) k_xinv(Work w, UserPtrs p, int use_ws) {
+__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
+    k_xinv(Work w, UserPtrs p, int use_ws, int lo_valid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
     const int b = blockIdx.x + p.blk0;
@@ -408,55 +646,70 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1) k_xinv(Work
     const int j0 = rb * rows;
     const int nx = G.nx, ny = G.ny;
     const int N1 = G.nx1, N2 = G.nx2, sstride = fft_seq_len(N1, N2);
+    const FDiv fN1 = G.fnx1, fN2 = G.fnx2, fmb = G.fmb, fnpair = G.fnpair, fnx = G.fnx;
     const int mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const cx<T> *spec = reinterpret_cast<const cx<T> *>(w.spec) + G.spec_off + (size_t)k * ncb * ny * mb;
     const int npair = rows >> 1;
     const int nload = ncb * npair * mb;
     for (int t = threadIdx.x; t < nload; t += blockDim.x) {
-        const int mm = t % mb;
-        const int rest = t / mb;
-        const int s = rest % npair, cb = rest / npair;
+        const int rest = (int)fdiv((unsigned)t, fmb);
+        const int mm = t - rest * mb;
+        const int cb = (int)fdiv((unsigned)rest, fnpair);
+        const int s_ = rest - cb * npair;
         const int m = cb * mb + mm;
         if (m >= nxh) continue;
-        const int ja = j0 + 2 * s, jb = ja + 1;
+        const int ja = j0 + 2 * s_, jb = ja + 1;
         cx<T> A_ = {(T)0, (T)0}, B_ = {(T)0, (T)0};
         if (ja < ny) A_ = spec[((size_t)cb * ny + ja) * mb + mm];
         if (jb < ny) B_ = spec[((size_t)cb * ny + jb) * mb + mm];
-        cx<T> *seq = buf + (size_t)s * sstride;
-        seq[fft_pos_tr(m, N1, N2)] = {A_.x - B_.y, A_.y + B_.x};
-        if (m > 0 && 2 * m < nx) seq[fft_pos_tr(nx - m, N1, N2)] = {A_.x + B_.y, B_.x - A_.y};
+        cx<T> *seq = buf + s_ * sstride;
+        seq[pos_tr(m, N1, N2, fN1)] = {A_.x - B_.y, A_.y + B_.x};
+        if (m > 0 && 2 * m < nx) seq[pos_tr(nx - m, N1, N2, fN1)] = {A_.x + B_.y, B_.x - A_.y};
     }
     __syncthreads();
     const cx<T> *twx = reinterpret_cast<const cx<T> *>(w.twx) + G.twx_off;
-    fft_batch<T, +1>(buf, npair, sstride, N1, N2, twx);
+    fft_batch<T, +1>(buf, npair, sstride, N1, N2, fN1, fN2, twx);
 
     const int gi = g - p.g0;
-    double *phi = use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi];
-    const size_t plane = (size_t)nx * ny;
-    const int ncell = rows * nx;
+    const ptrdiff_t plane = (ptrdiff_t)nx * ny;
+    const ptrdiff_t base = (ptrdiff_t)k * plane + (ptrdiff_t)j0 * nx;
+    const int ncell = min(rows, ny - j0) * nx;
+    double *phi64 = nullptr;
+    float *phh = nullptr, *phl = nullptr;
+    if (sizeof(T) == 8) phi64 = (use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi]) + base;
+    else {
+        phh = w.phi_hi + G.cell_off + base;
+        phl = w.phi_lo + G.cell_off + base;
+    }
     for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-        const int jl = t / nx, i = t - jl * nx;
-        const int j = j0 + jl;
-        if (j >= ny) continue;
-        const cx<T> z = buf[(size_t)(jl >> 1) * sstride + fft_pos_nat(i, N2)];
+        const int jl = (int)fdiv((unsigned)t, fnx), i = t - jl * nx;
+        const cx<T> z = buf[(jl >> 1) * sstride + pos_nat(i, fN2)];
         const T val = (jl & 1) ? z.y : z.x;
-        const size_t c = (size_t)k * plane + (size_t)j * nx + i;
-        if (IMODE == IM_STORE) {
-            if (sizeof(T) == 8) phi[c] = (double)val;
-            else phi[c] = f32_to_f64((float)val);
+        if constexpr (sizeof(T) == 8) {
+            phi64[t] = (double)val;
         } else {
-            phi[c] = A::store(A::add(A::load(phi[c]), A::from_f((float)val)));
+            if (IMODE == IM_STORE) {
+                phh[t] = (float)val;
+            } else {
+                const df cur = {phh[t], lo_valid ? phl[t] : 0.f};
+                const df nw = df_addf(cur, (float)val);
+                phh[t] = nw.hi;
+                phl[t] = nw.lo;
+            }
         }
     }
 }
 
 // ================================================================ k_correct
+constexpr int kRowGroupC = 2;
+
 // forward (ADJ = 0): u = u* + s rdx (phi_{i-1} - phi_i), v likewise,
-//                    w_k = w*_k + s rgzf_k (phi_{k-1} - phi_k), wall faces copied.
+//                    w_k = w*_k + s rgzf_k (phi_{k-1} - phi_k), wall faces copied;
+//                    mixed path: also writes phi (fp64) from its float-float value.
 // adjoint (ADJ = 1): g* = g_u + hz_k rdx (psi_{i-1} - psi_i), ...,
 //                    w_k = g_w,k + psi_{k-1} [k>=1] - psi_k [k<=nz-1].
 template <class A, int ADJ>
-__global__ void __launch_bounds__(kXThreads) k_correct(Work w, UserPtrs p, int use_ws, double s) {
+__global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, int use_ws, int lo_valid, double s) {
     typedef typename A::V V;
     const int b = blockIdx.x + p.blk0;
     const int g = find_grid(w.xblk_start, w.ngrids, b);
@@ -468,9 +721,19 @@ __global__ void __launch_bounds__(kXThreads) k_correct(Work w, UserPtrs p, int u
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     const int gi = g - p.g0;
     const int zo = G.z_off;
-    const double *phi = use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi];
-    const double *ui = p.in_u[gi], *vi = p.in_v[gi], *wi = p.in_w[gi];
-    double *uo = p.out_u[gi], *vo = p.out_v[gi], *wo = p.out_w[gi];
+    const ptrdiff_t plane = (ptrdiff_t)nx * ny;
+    const ptrdiff_t pbase = (ptrdiff_t)k * plane;
+    PhiSrc<A> ph;
+    constexpr bool MIX = IsDF<A>::value;
+    if constexpr (MIX) {
+        ph.hi = w.phi_hi + G.cell_off + pbase;
+        ph.lo = lo_valid ? w.phi_lo + G.cell_off + pbase : nullptr;
+    } else {
+        ph.p = (use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi]) + pbase;
+    }
+    const double *ui = p.in_u[gi] + pbase, *vi = p.in_v[gi] + pbase, *wi = p.in_w[gi] + pbase;
+    double *uo = p.out_u[gi] + pbase, *vo = p.out_v[gi] + pbase, *wo = p.out_w[gi] + pbase;
+    double *po = (MIX && !ADJ) ? p.out_p[gi] + pbase : nullptr;
     V cu, cv, cw;
     if (ADJ) {
         const double hz = w.z.hz[zo + k];
@@ -482,31 +745,67 @@ __global__ void __launch_bounds__(kXThreads) k_correct(Work w, UserPtrs p, int u
         cv = Coef<A>::c(s * G.rdy);
         cw = Coef<A>::c(s * w.z.rgzf[zo + k]);
     }
-    const size_t plane = (size_t)nx * ny;
-    const int ncell = rows * nx;
-    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-        const int jl = t / nx, i = t - jl * nx;
-        const int j = j0 + jl;
-        if (j >= ny) continue;
-        const int im = (i == 0) ? nx - 1 : i - 1;
-        const int jm = (j == 0) ? ny - 1 : j - 1;
-        const size_t c = (size_t)k * plane + (size_t)j * nx + i;
-        const V pc = A::load(__ldg(phi + c));
-        const V pim = A::load(__ldg(phi + (size_t)k * plane + (size_t)j * nx + im));
-        const V pjm = A::load(__ldg(phi + (size_t)k * plane + (size_t)jm * nx + i));
-        uo[c] = A::store(A::add(A::load(ui[c]), A::mul(cu, A::sub(pim, pc))));
-        vo[c] = A::store(A::add(A::load(vi[c]), A::mul(cv, A::sub(pjm, pc))));
-        if (ADJ) {
-            V dz = A::sub((k > 0) ? A::load(__ldg(phi + c - plane)) : A::zero(), pc);
-            wo[c] = A::store(A::add(A::load(wi[c]), dz));
-            if (k == nz - 1) wo[c + plane] = A::store(A::add(A::load(wi[c + plane]), pc));
-        } else {
-            if (k == 0) wo[c] = wi[c];
-            else {
-                const V pkm = A::load(__ldg(phi + c - plane));
-                wo[c] = A::store(A::add(A::load(wi[c]), A::mul(cw, A::sub(pkm, pc))));
+    const int lane = threadIdx.x & 31;
+    const SegMap sm = seg_map(nx, rows);
+    for (int seg = sm.seg0; seg < sm.nseg; seg += sm.segstep) {
+        const int i = seg * 32 + lane;
+        const bool act = i < nx;
+        const int ii = act ? i : nx - 1;
+        const int im = (ii == 0) ? nx - 1 : ii - 1;
+        const bool own_dn = (lane == 0) || (ii == 0);
+        V Pjm = A::zero();
+        bool have = false;
+        for (int jg = sm.r0; jg < sm.r1; jg += kRowGroupC) {
+            V pc[kRowGroupC], pkm[kRowGroupC], ped[kRowGroupC];
+            double ru[kRowGroupC], rv[kRowGroupC], rw[kRowGroupC], rwt[kRowGroupC];
+            V pjm0 = A::zero();
+            const bool need0 = !have;
+#pragma unroll
+            for (int q = 0; q < kRowGroupC; ++q) {
+                const int jl = jg + q, j = j0 + jl;
+                pc[q] = pkm[q] = ped[q] = A::zero();
+                ru[q] = rv[q] = rw[q] = rwt[q] = 0.0;
+                if (jl < sm.r1 && j < ny) {
+                    const int jm = (j == 0) ? ny - 1 : j - 1;
+                    const int row = j * nx;
+                    if (q == 0 && need0) pjm0 = ph.get(jm * nx + ii);
+                    pc[q] = ph.get(row + ii);
+                    if (k > 0) pkm[q] = ph.get(row + ii - plane);
+                    if (own_dn) ped[q] = ph.get(row + im);
+                    if (act) {
+                        ru[q] = ui[row + i];
+                        rv[q] = vi[row + i];
+                        rw[q] = wi[row + i];
+                        if (k == nz - 1) rwt[q] = wi[row + i + plane];
+                    }
+                }
             }
-            if (k == nz - 1) wo[c + plane] = wi[c + plane];
+            if (need0) Pjm = pjm0;
+#pragma unroll
+            for (int q = 0; q < kRowGroupC; ++q) {
+                const int jl = jg + q, j = j0 + jl;
+                if (jl >= sm.r1 || j >= ny) break;  // warp-uniform
+                const int row = j * nx;
+                const V Pc = pc[q];
+                V Pim = shup(Pc, 1);
+                if (own_dn) Pim = ped[q];
+                if (act) {
+                    const int c = row + i;
+                    uo[c] = A::store(A::add(A::load(ru[q]), A::mul(cu, A::sub(Pim, Pc))));
+                    vo[c] = A::store(A::add(A::load(rv[q]), A::mul(cv, A::sub(Pjm, Pc))));
+                    if (ADJ) {
+                        wo[c] = A::store(A::add(A::load(rw[q]), A::sub(pkm[q], Pc)));
+                        if (k == nz - 1) wo[c + plane] = A::store(A::add(A::load(rwt[q]), Pc));
+                    } else {
+                        if (k == 0) wo[c] = rw[q];
+                        else wo[c] = A::store(A::add(A::load(rw[q]), A::mul(cw, A::sub(pkm[q], Pc))));
+                        if (k == nz - 1) wo[c + plane] = rwt[q];
+                        if (po) po[c] = A::store(Pc);
+                    }
+                }
+                Pjm = Pc;
+                have = true;
+            }
         }
     }
 }
@@ -525,22 +824,21 @@ __global__ void __launch_bounds__(kXThreads) k_divstat(Work w, UserPtrs p) {
     const int j0 = rb * rows;
     const int nx = G.nx, ny = G.ny;
     const int gi = g - p.g0;
-    const double *u = p.out_u[gi], *vv = p.out_v[gi], *ww = p.out_w[gi];
+    const ptrdiff_t plane = (ptrdiff_t)nx * ny;
+    const ptrdiff_t pbase = (ptrdiff_t)k * plane;
+    const double *u = p.out_u[gi] + pbase, *vv = p.out_v[gi] + pbase, *ww = p.out_w[gi] + pbase;
     const V cu = Coef<A>::c(G.rdx), cv = Coef<A>::c(G.rdy), cw = Coef<A>::c(w.z.rhz[G.z_off + k]);
-    const size_t plane = (size_t)nx * ny;
     float mx = 0.f;
-    const int ncell = rows * nx;
+    const int ncell = min(rows, ny - j0) * nx;
     for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-        const int jl = t / nx, i = t - jl * nx;
+        const int jl = (int)fdiv((unsigned)t, G.fnx), i = t - jl * nx;
         const int j = j0 + jl;
-        if (j >= ny) continue;
         const int ip = (i + 1 == nx) ? 0 : i + 1;
         const int jp = (j + 1 == ny) ? 0 : j + 1;
-        const size_t c = (size_t)k * plane + (size_t)j * nx + i;
-        const size_t rowk = (size_t)k * plane + (size_t)j * nx;
-        V d = A::mul(cu, A::sub(A::load(u[rowk + ip]), A::load(u[rowk + i])));
-        d = A::add(d, A::mul(cv, A::sub(A::load(vv[(size_t)k * plane + (size_t)jp * nx + i]), A::load(vv[c]))));
-        d = A::add(d, A::mul(cw, A::sub(A::load(ww[c + plane]), A::load(ww[c]))));
+        const int row = j * nx;
+        V d = A::mul(cu, A::sub(A::load(u[row + ip]), A::load(u[row + i])));
+        d = A::add(d, A::mul(cv, A::sub(A::load(vv[jp * nx + i]), A::load(vv[row + i]))));
+        d = A::add(d, A::mul(cw, A::sub(A::load(ww[plane + row + i]), A::load(ww[row + i]))));
         const float a = absv<A>(d);
         mx = (a > mx || a != a) ? a : mx;
     }
@@ -592,17 +890,23 @@ __global__ void __launch_bounds__(256) k_build_table(Work w) {
 // ================================================================ launchers
 static inline dim3 grid1(int n) { return dim3((unsigned)n); }
 
-cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int nblk, double s,
-                        double rs, size_t smem, cudaStream_t st) {
+cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
+                        double s, double rs, size_t smem, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
     if (mixed) {
-        if (mode == XM_DIV) k_xfwd<float, DFArith, XM_DIV><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, s, rs);
-        else if (mode == XM_RESID) k_xfwd<float, DFArith, XM_RESID><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, s, rs);
-        else k_xfwd<float, DFArith, XM_ADJ><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, s, rs);
+        if (mode == XM_DIV)
+            k_xfwd<float, DFArith, XM_DIV><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        else if (mode == XM_RESID)
+            k_xfwd<float, DFArith, XM_RESID><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        else
+            k_xfwd<float, DFArith, XM_ADJ><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
     } else {
-        if (mode == XM_DIV) k_xfwd<double, F64Arith, XM_DIV><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, s, rs);
-        else if (mode == XM_ADJ) k_xfwd<double, F64Arith, XM_ADJ><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, s, rs);
-        else return cudaErrorInvalidValue;
+        if (mode == XM_DIV)
+            k_xfwd<double, F64Arith, XM_DIV><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        else if (mode == XM_ADJ)
+            k_xfwd<double, F64Arith, XM_ADJ><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        else
+            return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
@@ -626,27 +930,29 @@ cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int nblk, size_t smem,
-                        cudaStream_t st) {
+cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
+                        size_t smem, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
     if (mixed) {
-        if (mode == IM_STORE) k_xinv<float, DFArith, IM_STORE><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws);
-        else k_xinv<float, DFArith, IM_ACCUM><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws);
+        if (mode == IM_STORE)
+            k_xinv<float, DFArith, IM_STORE><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+        else
+            k_xinv<float, DFArith, IM_ACCUM><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
     } else {
-        k_xinv<double, F64Arith, IM_STORE><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws);
+        k_xinv<double, F64Arith, IM_STORE><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int nblk, double s,
-                           cudaStream_t st) {
+cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
+                           int nblk, double s, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
     if (mixed) {
-        if (adjoint) k_correct<DFArith, 1><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, s);
-        else k_correct<DFArith, 0><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, s);
+        if (adjoint) k_correct<DFArith, 1><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
+        else k_correct<DFArith, 0><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
     } else {
-        if (adjoint) k_correct<F64Arith, 1><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, s);
-        else k_correct<F64Arith, 0><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, s);
+        if (adjoint) k_correct<F64Arith, 1><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
+        else k_correct<F64Arith, 0><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
     }
     return cudaGetLastError();
 }

@@ -94,6 +94,16 @@ def uniform_torch(seed: int, array_id: int, shape, lo=-1.0, hi=1.0, device="cpu"
     return (lo + (hi - lo) * u01).reshape(tuple(shape))
 
 
+def normal_torch(seed: int, array_id: int, shape, device="cpu"):
+    """Same stream as normal_np (Box-Muller on two uniform streams), as torch float64."""
+    import torch
+    n = int(np.prod(shape))
+    u1 = ((bits_torch(seed, array_id, n, device=device) >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+    u2 = ((bits_torch(seed, array_id | 0x80, n, device=device) >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+    r = torch.sqrt(-2.0 * torch.log1p(-u1))
+    return (r * torch.cos(2.0 * np.pi * u2)).reshape(tuple(shape))
+
+
 # ---------------------------------------------------------------------------
 # staggered field shapes: u [nz][ny][nxu], v [nz][nyv][nx], w [nz+1][ny][nx]
 # nxu = nx (periodic x) or nx+1 (wall x);  nyv likewise.

@@ -11,6 +11,9 @@ def test_numpy_torch_streams_identical():
         a = synth.bits_np(seed, aid, 4096, start=123)
         b = synth.bits_torch(seed, aid, 4096, start=123).numpy().view(np.uint64)
         assert np.array_equal(a, b)
+        na = synth.normal_np(seed, aid, (64,))
+        nb = synth.normal_torch(seed, aid, (64,)).numpy()
+        assert np.max(np.abs(na - nb)) < 1e-12
         ua = synth.uniform_np(seed, aid, (16, 16))
         ub = synth.uniform_torch(seed, aid, (16, 16)).numpy()
         assert np.array_equal(ua, ub)
