@@ -268,7 +268,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
         pl->total_cells += (long long)d.nx * d.ny * d.nz;
     }
     if (maxx > (size_t)prop.sharedMemPerBlockOptin || maxyz > (size_t)prop.sharedMemPerBlockOptin ||
-        (size_t)pl->maxnz * 8 > (size_t)prop.sharedMemPerBlockOptin)
+        (size_t)10 * (pl->maxnz + 1) * 8 > (size_t)prop.sharedMemPerBlockOptin)
         return IBF_ERR_UNSUPPORTED_SIZE;
     pl->xsmem = maxx;
     pl->yzsmem = maxyz;
@@ -391,7 +391,10 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
     e = cudaMemset(w.mean_b, 0, sizeof(double) * ngrids);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
 
-    e = set_smem_limits(mixed, pl->xsmem, pl->yzsmem);
+    // the attribute is a per-kernel cap shared by every plan: set it to the device maximum
+    // so that no later plan can lower it under an earlier plan's launch size
+    const size_t cap = (size_t)prop.sharedMemPerBlockOptin;
+    e = set_smem_limits(mixed, cap, cap, cap);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     e = launch_build_table(mixed, w, pl->nyzblk, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "pivot table kernel");

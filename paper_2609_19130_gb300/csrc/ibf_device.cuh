@@ -141,6 +141,7 @@ struct F64Arith {
     __device__ __forceinline__ static V mul(V a, V b) { return a * b; }
     __device__ __forceinline__ static V from_f(float a) { return (double)a; }
     __device__ __forceinline__ static V zero() { return 0.0; }
+    __device__ __forceinline__ static V norm(V a) { return a; }
 };
 struct DFArith {
     typedef df V;
@@ -151,6 +152,7 @@ struct DFArith {
     __device__ __forceinline__ static V mul(V a, V b) { return df_mul(a, b); }
     __device__ __forceinline__ static V from_f(float a) { return df_make(a); }
     __device__ __forceinline__ static V zero() { return df_make(0.f); }
+    __device__ __forceinline__ static V norm(V a) { return quick_two_sum(a.hi, a.lo); }
 };
 
 // ------------------------------------------------------------------ twiddle constants
@@ -203,90 +205,76 @@ template <typename T, int DIR> struct Bfly<T, 4, DIR> {
     }
 };
 
-// One Stockham autosort stage of radix R over P registers; NS = product of the
-// radices of the previous stages.  Output in natural order after the last stage.
-template <typename T, int P, int R, int NS, int DIR>
-__device__ __forceinline__ void stockham_stage(const cx<T> *x, cx<T> *y) {
-#pragma unroll
-    for (int j = 0; j < P / R; ++j) {
-        const int k = j % NS;
-        cx<T> v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            v[r] = x[j + r * (P / R)];
-            if (NS > 1 && r > 0 && k > 0) {
-                cx<T> w = Tw96<T>::get((r * k * (96 / (NS * R))) % 96);
-                if (DIR > 0) w.y = -w.y;
-                v[r] = cmul(v[r], w);
-            }
-        }
-        Bfly<T, R, DIR>::run(v);
-        const int idx = (j / NS) * NS * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) y[idx + r * NS] = v[r];
-    }
+// In-place register DFT of the P elements x[s * STRIDE], s < P (P a divisor of 96
+// built from radices 2, 3, 4): P = P1 * P2 with P1 the first radix, DFT_P1 on the
+// P2 strided subsets, twiddles w_P^(n2 k1), DFT_P2 on the P1 contiguous groups
+// (the "four-step" factorisation applied inside the registers).  No second array
+// is needed; output k is left at x[ip_rev(P, k) * STRIDE], a digit permutation
+// that the callers apply when they store.
+__host__ __device__ constexpr int ip_first(int P) { return P == 6 ? 2 : (P % 4 == 0 ? 4 : (P % 2 == 0 ? 2 : 3)); }
+__host__ __device__ constexpr int ip_rev(int P, int k) {
+    return P <= 4 ? k : (P / ip_first(P)) * (k % ip_first(P)) + ip_rev(P / ip_first(P), k / ip_first(P));
 }
 
-// Register DFT of length P (in place on x[0..P-1]).
-template <typename T, int P, int DIR> struct RegDFT;
-template <typename T, int DIR> struct RegDFT<T, 1, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *) {}
-};
-template <typename T, int DIR> struct RegDFT<T, 2, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) { Bfly<T, 2, DIR>::run(x); }
-};
-template <typename T, int DIR> struct RegDFT<T, 3, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) { Bfly<T, 3, DIR>::run(x); }
-};
-template <typename T, int DIR> struct RegDFT<T, 4, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) { Bfly<T, 4, DIR>::run(x); }
-};
-template <typename T, int DIR> struct RegDFT<T, 6, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) {
-        cx<T> y[6];
-        stockham_stage<T, 6, 2, 1, DIR>(x, y);
-        stockham_stage<T, 6, 3, 2, DIR>(y, x);
-    }
-};
-template <typename T, int DIR> struct RegDFT<T, 8, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) {
-        cx<T> y[8];
-        stockham_stage<T, 8, 4, 1, DIR>(x, y);
-        stockham_stage<T, 8, 2, 4, DIR>(y, x);
-    }
-};
-template <typename T, int DIR> struct RegDFT<T, 12, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) {
-        cx<T> y[12];
-        stockham_stage<T, 12, 4, 1, DIR>(x, y);
-        stockham_stage<T, 12, 3, 4, DIR>(y, x);
-    }
-};
-template <typename T, int DIR> struct RegDFT<T, 16, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) {
-        cx<T> y[16];
-        stockham_stage<T, 16, 4, 1, DIR>(x, y);
-        stockham_stage<T, 16, 4, 4, DIR>(y, x);
-    }
-};
-template <typename T, int DIR> struct RegDFT<T, 24, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) {
-        cx<T> y[24];
-        stockham_stage<T, 24, 4, 1, DIR>(x, y);
-        stockham_stage<T, 24, 2, 4, DIR>(y, x);
-        stockham_stage<T, 24, 3, 8, DIR>(x, y);
+template <typename T, int N, int P, int OFF, int STRIDE, int DIR> struct IPDFT {
+    __device__ __forceinline__ static void run(cx<T> (&x)[N]) {
+        constexpr int P1 = ip_first(P), P2 = P / P1;
+        IPDFT_subsets<0, P2>(x);
 #pragma unroll
-        for (int i = 0; i < 24; ++i) x[i] = y[i];
+        for (int n2 = 1; n2 < P2; ++n2) {
+#pragma unroll
+            for (int k1 = 1; k1 < P1; ++k1) {
+                cx<T> w = Tw96<T>::get((n2 * k1 * (96 / P)) % 96);
+                if (DIR > 0) w.y = -w.y;
+                const int e = OFF + (n2 + P2 * ip_rev(P1, k1)) * STRIDE;
+                x[e] = cmul(x[e], w);
+            }
+        }
+        IPDFT_groups<0, P1>(x);
+    }
+    // DFT_P1 on the P2 strided subsets n2 + P2 n1
+    template <int n2, int P2> __device__ __forceinline__ static void IPDFT_subsets(cx<T> (&x)[N]) {
+        if constexpr (n2 < P2) {
+            IPDFT<T, N, ip_first(P), OFF + n2 * STRIDE, STRIDE * P2, DIR>::run(x);
+            IPDFT_subsets<n2 + 1, P2>(x);
+        }
+    }
+    // DFT_P2 on the P1 contiguous groups
+    template <int r, int P1> __device__ __forceinline__ static void IPDFT_groups(cx<T> (&x)[N]) {
+        if constexpr (r < P1) {
+            IPDFT<T, N, P / P1, OFF + (P / P1) * r * STRIDE, STRIDE, DIR>::run(x);
+            IPDFT_groups<r + 1, P1>(x);
+        }
     }
 };
-template <typename T, int DIR> struct RegDFT<T, 32, DIR> {
-    __device__ __forceinline__ static void run(cx<T> *x) {
-        cx<T> y[32];
-        stockham_stage<T, 32, 4, 1, DIR>(x, y);
-        stockham_stage<T, 32, 4, 4, DIR>(y, x);
-        stockham_stage<T, 32, 2, 16, DIR>(x, y);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = y[i];
+template <typename T, int N, int OFF, int STRIDE, int DIR> struct IPDFT<T, N, 1, OFF, STRIDE, DIR> {
+    __device__ __forceinline__ static void run(cx<T> (&)[N]) {}
+};
+template <typename T, int N, int OFF, int STRIDE, int DIR> struct IPDFT<T, N, 2, OFF, STRIDE, DIR> {
+    __device__ __forceinline__ static void run(cx<T> (&x)[N]) {
+        cx<T> v[2] = {x[OFF], x[OFF + STRIDE]};
+        Bfly<T, 2, DIR>::run(v);
+        x[OFF] = v[0];
+        x[OFF + STRIDE] = v[1];
+    }
+};
+template <typename T, int N, int OFF, int STRIDE, int DIR> struct IPDFT<T, N, 3, OFF, STRIDE, DIR> {
+    __device__ __forceinline__ static void run(cx<T> (&x)[N]) {
+        cx<T> v[3] = {x[OFF], x[OFF + STRIDE], x[OFF + 2 * STRIDE]};
+        Bfly<T, 3, DIR>::run(v);
+        x[OFF] = v[0];
+        x[OFF + STRIDE] = v[1];
+        x[OFF + 2 * STRIDE] = v[2];
+    }
+};
+template <typename T, int N, int OFF, int STRIDE, int DIR> struct IPDFT<T, N, 4, OFF, STRIDE, DIR> {
+    __device__ __forceinline__ static void run(cx<T> (&x)[N]) {
+        cx<T> v[4] = {x[OFF], x[OFF + STRIDE], x[OFF + 2 * STRIDE], x[OFF + 3 * STRIDE]};
+        Bfly<T, 4, DIR>::run(v);
+        x[OFF] = v[0];
+        x[OFF + STRIDE] = v[1];
+        x[OFF + 2 * STRIDE] = v[2];
+        x[OFF + 3 * STRIDE] = v[3];
     }
 };
 
@@ -315,19 +303,31 @@ template <> __device__ __forceinline__ cx<double> ld_tw<double>(const cx<double>
     return {v.x, v.y};
 }
 
+// store DFT outputs q = Q..P-1 (held at x[ip_rev(P, q)]) to base[q * ld], optionally
+// multiplied by tw[q * tstep] (conjugated when CONJ); compile-time recursion so that
+// every register index is a constant
+template <typename T, int P, int Q, bool TWID, bool CONJ>
+__device__ __forceinline__ void ip_store(cx<T> (&x)[P], cx<T> *base, int ld, const cx<T> *tw, int tstep) {
+    if constexpr (Q < P) {
+        cx<T> v = x[ip_rev(P, Q)];
+        if constexpr (TWID && Q > 0) {
+            const cx<T> t = ld_tw<T>(tw, Q * tstep);
+            v = CONJ ? cmulc(v, t) : cmul(v, t);
+        }
+        base[Q * ld] = v;
+        ip_store<T, P, Q + 1, TWID, CONJ>(x, base, ld, tw, tstep);
+    }
+}
+
 // column task: DFT_N1 down column c of one sequence (P == N1); forward multiplies by w_N^(c q1)
 template <typename T, int P, int DIR>
 __device__ __forceinline__ void fft_col_task(cx<T> *seq, int c, int ld, const cx<T> *tw) {
     cx<T> x[P];
 #pragma unroll
     for (int r = 0; r < P; ++r) x[r] = seq[r * ld + c];
-    RegDFT<T, P, DIR>::run(x);
-    if (DIR < 0 && c > 0) {
-#pragma unroll
-        for (int r = 1; r < P; ++r) x[r] = cmul(x[r], ld_tw<T>(tw, c * r));
-    }
-#pragma unroll
-    for (int r = 0; r < P; ++r) seq[r * ld + c] = x[r];
+    IPDFT<T, P, P, 0, 1, DIR>::run(x);
+    if (DIR < 0 && c > 0) ip_store<T, P, 0, true, false>(x, seq + c, ld, tw, c);
+    else ip_store<T, P, 0, false, false>(x, seq + c, ld, tw, 0);
 }
 // row task: DFT_N2 along row q1 of one sequence (P == N2); inverse then multiplies by w_N^-(p2 q1)
 template <typename T, int P, int DIR>
@@ -336,13 +336,9 @@ __device__ __forceinline__ void fft_row_task(cx<T> *seq, int q1, int ld, const c
     cx<T> *row = seq + q1 * ld;
 #pragma unroll
     for (int c = 0; c < P; ++c) x[c] = row[c];
-    RegDFT<T, P, DIR>::run(x);
-    if (DIR > 0 && q1 > 0) {
-#pragma unroll
-        for (int c = 1; c < P; ++c) x[c] = cmulc(x[c], ld_tw<T>(tw, c * q1));
-    }
-#pragma unroll
-    for (int c = 0; c < P; ++c) row[c] = x[c];
+    IPDFT<T, P, P, 0, 1, DIR>::run(x);
+    if (DIR > 0 && q1 > 0) ip_store<T, P, 0, true, true>(x, row, 1, tw, q1);
+    else ip_store<T, P, 0, false, false>(x, row, 1, tw, 0);
 }
 
 __device__ __forceinline__ unsigned fdiv(unsigned n, const FDiv &f) { return (__umulhi(n, f.m) + n) >> f.s; }

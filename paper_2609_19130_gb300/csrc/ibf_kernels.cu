@@ -572,11 +572,17 @@ __global__ void __launch_bounds__(kYZThreads) k_yzbwd(Work w) {
 // ================================================================ k_00 (fp64, one CTA per grid)
 template <typename T>
 __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
-    extern __shared__ double rhs[];  // nz entries
+    // Shared memory: right-hand side, hz, and two copies (ping-pong) of the four PCR
+    // arrays a, b, c, d; every array has nz+1 entries.
+    extern __shared__ double sh00[];
     __shared__ double red[8];
     const int g = blockIdx.x;
     const GridDev &G = w.grids[g];
     const int nz = G.nz, nrb = G.nrb, zo = G.z_off;
+    const int L = nz + 1;
+    double *rhs = sh00, *hz = sh00 + L;
+    double *A0 = sh00 + 2 * L, *B0 = A0 + L, *C0 = B0 + L, *D0 = C0 + L;
+    double *A1 = D0 + L, *B1 = A1 + L, *C1 = B1 + L, *D1 = C1 + L;
     const double *part = w.partial + G.part_off;
     double loc = 0.0, locp = 0.0;
     bool bad = false;
@@ -585,12 +591,14 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
         for (int r = 0; r < nrb; ++r) S += part[k * nrb + r];
         const double m = S * G.inv_nxy;  // plane mean of the right-hand side
         if (!isfinite(m)) bad = true;
+        const double h = w.z.hz[zo + k];
         rhs[k] = m;
-        loc += w.z.hz[zo + k] * m;
+        hz[k] = h;
+        loc += h * m;
         if (!first_solve) {
             double P = 0.0;
             for (int r = 0; r < nrb; ++r) P += w.partial_phi[G.part_off + k * nrb + r];
-            locp += w.z.hz[zo + k] * P * G.inv_nxy;
+            locp += h * P * G.inv_nxy;
         }
     }
     if (bad) atomicOr(w.err, 1u << 6);  // IBF_ERR_NONFINITE
@@ -599,33 +607,66 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     // weighted mean of the phi being refined: the correction also removes it, so that
     // phi + delta keeps a zero weighted mean (L cannot see a constant)
     const double totp = first_solve ? 0.0 : Red<F64Arith>::sum(locp, red);
-    if (threadIdx.x == 0) {
-        const double mean = tot / G.sum_hz;
-        if (first_solve) {
-            w.mean_b[g] = mean;
-            double scale = 0.0;
-            for (int k = 0; k < nz; ++k) scale = fmax(scale, fabs(rhs[k]));
-            // compatibility defect large compared with the plane means -> warning
-            if (fabs(mean) > 1e-8 * scale && fabs(mean) > 0.0) atomicOr(w.err, 1u << 7);
-        }
-        // pinned Thomas: level 0 fixed to zero (inv00_0 = 0), rows 1..nz-1
-        const double *az = w.z.az + zo, *cz = w.z.cz + zo, *iv = w.z.inv00 + zo;
-        double d = 0.0;
-        for (int k = 0; k < nz; ++k) {
-            d = (rhs[k] - mean - az[k] * d) * iv[k];
-            rhs[k] = d;
-        }
-        double nx_ = 0.0, sv = 0.0;
-        for (int k = nz - 1; k >= 0; --k) {
-            nx_ = rhs[k] - cz[k] * iv[k] * nx_;
-            rhs[k] = nx_;
-            sv += w.z.hz[zo + k] * nx_;
-        }
-        const double mphi = (sv + totp) / G.sum_hz;
-        cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
-        const size_t stride = (size_t)G.ncb * G.ny * G.mb;
-        for (int k = 0; k < nz; ++k) spec[(size_t)k * stride] = {(T)(rhs[k] - mphi), (T)0};
+    if (threadIdx.x == 0) red[0] = tot / G.sum_hz;
+    __syncthreads();
+    const double mean = red[0];
+    if (threadIdx.x == 0 && first_solve) {
+        w.mean_b[g] = mean;
+        double scale = 0.0;
+        for (int k = 0; k < nz; ++k) scale = fmax(scale, fabs(rhs[k]));
+        // compatibility defect large compared with the plane means -> warning
+        if (fabs(mean) > 1e-8 * scale && fabs(mean) > 0.0) atomicOr(w.err, 1u << 7);
     }
+    // Pinned system (level 0 fixed to zero, so row 0 reads phi_0 = 0) solved by
+    // parallel cyclic reduction (Hockney 1965): each step eliminates from every row its
+    // couplings at distance st; after ceil(log2 nz) steps row k reads phi_k = d_k / b_k.
+    // Row k of L along z: a = az_k (to k-1), b = -(az_k + cz_k), c = cz_k (to k+1).
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        if (k == 0) { A0[k] = 0.0; B0[k] = 1.0; C0[k] = 0.0; D0[k] = 0.0; }
+        else {
+            const double a = w.z.az[zo + k], c = w.z.cz[zo + k];
+            A0[k] = a; B0[k] = -(a + c); C0[k] = (k == 0) ? 0.0 : c; D0[k] = rhs[k] - mean;
+        }
+    }
+    __syncthreads();
+    for (int st = 1; st < nz; st <<= 1) {
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+            double na = 0.0, nb = B0[k], nc = 0.0, nd = D0[k];
+            if (k - st >= 0) {
+                const double al = -A0[k] / B0[k - st];
+                na = al * A0[k - st];
+                nb += al * C0[k - st];
+                nd += al * D0[k - st];
+            }
+            if (k + st < nz) {
+                const double ga = -C0[k] / B0[k + st];
+                nc = ga * C0[k + st];
+                nb += ga * A0[k + st];
+                nd += ga * D0[k + st];
+            }
+            A1[k] = na; B1[k] = nb; C1[k] = nc; D1[k] = nd;
+        }
+        __syncthreads();
+        double *t;
+        t = A0; A0 = A1; A1 = t;
+        t = B0; B0 = B1; B1 = t;
+        t = C0; C0 = C1; C1 = t;
+        t = D0; D0 = D1; D1 = t;
+    }
+    double lsv = 0.0;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        const double ph = D0[k] / B0[k];
+        rhs[k] = ph;
+        lsv += hz[k] * ph;
+    }
+    __syncthreads();
+    const double sv = Red<F64Arith>::sum(lsv, red);
+    if (threadIdx.x == 0) rhs[nz] = (sv + totp) / G.sum_hz;  // weighted mean to remove
+    __syncthreads();
+    const double mphi = rhs[nz];
+    cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
+    const size_t stride = (size_t)G.ncb * G.ny * G.mb;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) spec[(size_t)k * stride] = {(T)(rhs[k] - mphi), (T)0};
 }
 
 // ================================================================ k_xinv
@@ -690,8 +731,10 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
         } else {
             if (IMODE == IM_STORE) {
                 phh[t] = (float)val;
+            } else if (!lo_valid) {
+                phl[t] = (float)val;  // phi = phi_0 + delta held as the unevaluated pair (hi, lo)
             } else {
-                const df cur = {phh[t], lo_valid ? phl[t] : 0.f};
+                const df cur = {phh[t], phl[t]};
                 const df nw = df_addf(cur, (float)val);
                 phh[t] = nw.hi;
                 phl[t] = nw.lo;
@@ -800,7 +843,7 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
                         if (k == 0) wo[c] = rw[q];
                         else wo[c] = A::store(A::add(A::load(rw[q]), A::mul(cw, A::sub(pkm[q], Pc))));
                         if (k == nz - 1) wo[c + plane] = rwt[q];
-                        if (po) po[c] = A::store(Pc);
+                        if (po) po[c] = A::store(A::norm(Pc));
                     }
                 }
                 Pjm = Pc;
@@ -924,7 +967,7 @@ cudaError_t launch_yzbwd(int mixed, const Work &w, int nblk, size_t smem, cudaSt
 }
 
 cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cudaStream_t st) {
-    const size_t smem = (size_t)maxnz * sizeof(double);
+    const size_t smem = (size_t)10 * (maxnz + 1) * sizeof(double);
     if (mixed) k_00<float><<<w.ngrids, 256, smem, st>>>(w, first_solve);
     else k_00<double><<<w.ngrids, 256, smem, st>>>(w, first_solve);
     return cudaGetLastError();
@@ -976,7 +1019,7 @@ cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t set_smem_limits(int mixed, size_t xsmem, size_t yzsmem) {
+cudaError_t set_smem_limits(int mixed, size_t xsmem, size_t yzsmem, size_t smem00) {
     cudaError_t e = cudaSuccess;
 #define IBF_ATTR(kern, bytes) \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
@@ -988,12 +1031,14 @@ cudaError_t set_smem_limits(int mixed, size_t xsmem, size_t yzsmem) {
         IBF_ATTR((k_xinv<float, DFArith, IM_ACCUM>), xsmem)
         IBF_ATTR(k_yzfwd<float>, yzsmem)
         IBF_ATTR(k_yzbwd<float>, yzsmem)
+        IBF_ATTR(k_00<float>, smem00)
     } else {
         IBF_ATTR((k_xfwd<double, F64Arith, XM_DIV>), xsmem)
         IBF_ATTR((k_xfwd<double, F64Arith, XM_ADJ>), xsmem)
         IBF_ATTR((k_xinv<double, F64Arith, IM_STORE>), xsmem)
         IBF_ATTR(k_yzfwd<double>, yzsmem)
         IBF_ATTR(k_yzbwd<double>, yzsmem)
+        IBF_ATTR(k_00<double>, smem00)
     }
 #undef IBF_ATTR
     return e;
