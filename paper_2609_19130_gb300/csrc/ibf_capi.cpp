@@ -24,6 +24,7 @@ thread_local std::string g_last_error;
 
 ibf_status cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();  // do not leave a non-sticky error pending for the caller's next CUDA call
     return IBF_ERR_CUDA;
 }
 
@@ -391,10 +392,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
     e = cudaMemset(w.mean_b, 0, sizeof(double) * ngrids);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
 
-    // the attribute is a per-kernel cap shared by every plan: set it to the device maximum
-    // so that no later plan can lower it under an earlier plan's launch size
-    const size_t cap = (size_t)prop.sharedMemPerBlockOptin;
-    e = set_smem_limits(mixed, cap, cap, cap);
+    e = set_smem_limits(mixed);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     e = launch_build_table(mixed, w, pl->nyzblk, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "pivot table kernel");

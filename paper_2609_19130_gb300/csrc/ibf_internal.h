@@ -95,6 +95,6 @@ cudaError_t launch_divstat(int mixed, const Work &w, const UserPtrs &p, int nblk
 cudaError_t launch_finalize(const Work &w, double *max_div, double *max_div_in, double *compat, double s,
                             cudaStream_t st);
 cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t st);
-cudaError_t set_smem_limits(int mixed, size_t xsmem, size_t yzsmem, size_t smem00);
+cudaError_t set_smem_limits(int mixed);
 
 }  // namespace ibf

@@ -1019,28 +1019,37 @@ cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t set_smem_limits(int mixed, size_t xsmem, size_t yzsmem, size_t smem00) {
-    cudaError_t e = cudaSuccess;
-#define IBF_ATTR(kern, bytes) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
+// Dynamic shared-memory caps are per-kernel attributes shared by every plan in the
+// process: each is set to the device's opt-in maximum minus the kernel's static shared
+// memory, so that no plan can lower them under another plan's launch size.
+cudaError_t set_smem_limits(int mixed) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    auto set = [&](const void *fn) {
+        if (e != cudaSuccess) return;
+        cudaFuncAttributes a;
+        e = cudaFuncGetAttributes(&a, fn);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+    };
     if (mixed) {
-        IBF_ATTR((k_xfwd<float, DFArith, XM_DIV>), xsmem)
-        IBF_ATTR((k_xfwd<float, DFArith, XM_RESID>), xsmem)
-        IBF_ATTR((k_xfwd<float, DFArith, XM_ADJ>), xsmem)
-        IBF_ATTR((k_xinv<float, DFArith, IM_STORE>), xsmem)
-        IBF_ATTR((k_xinv<float, DFArith, IM_ACCUM>), xsmem)
-        IBF_ATTR(k_yzfwd<float>, yzsmem)
-        IBF_ATTR(k_yzbwd<float>, yzsmem)
-        IBF_ATTR(k_00<float>, smem00)
+        set((const void *)k_xfwd<float, DFArith, XM_DIV>);
+        set((const void *)k_xfwd<float, DFArith, XM_RESID>);
+        set((const void *)k_xfwd<float, DFArith, XM_ADJ>);
+        set((const void *)k_xinv<float, DFArith, IM_STORE>);
+        set((const void *)k_xinv<float, DFArith, IM_ACCUM>);
+        set((const void *)k_yzfwd<float>);
+        set((const void *)k_yzbwd<float>);
+        set((const void *)k_00<float>);
     } else {
-        IBF_ATTR((k_xfwd<double, F64Arith, XM_DIV>), xsmem)
-        IBF_ATTR((k_xfwd<double, F64Arith, XM_ADJ>), xsmem)
-        IBF_ATTR((k_xinv<double, F64Arith, IM_STORE>), xsmem)
-        IBF_ATTR(k_yzfwd<double>, yzsmem)
-        IBF_ATTR(k_yzbwd<double>, yzsmem)
-        IBF_ATTR(k_00<double>, smem00)
+        set((const void *)k_xfwd<double, F64Arith, XM_DIV>);
+        set((const void *)k_xfwd<double, F64Arith, XM_ADJ>);
+        set((const void *)k_xinv<double, F64Arith, IM_STORE>);
+        set((const void *)k_yzfwd<double>);
+        set((const void *)k_yzbwd<double>);
+        set((const void *)k_00<double>);
     }
-#undef IBF_ATTR
     return e;
 }
 
