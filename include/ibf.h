@@ -165,6 +165,32 @@ ibf_status ibf_profile_enable(ibf_plan *plan, int enable);
 int ibf_profile_read(ibf_plan *plan, const char **names, long long *launches, double *ms, int cap);
 ibf_status ibf_profile_reset(ibf_plan *plan);
 
+/* ------------------------------------------------------------------------------
+ * Projection without any device allocation (the paper has no counterpart; this is
+ * a service of this library).
+ *
+ * For callers that may not allocate device memory when they project: a host
+ * framework whose own allocator owns all of the GPU's memory, code running where an
+ * allocation would synchronise the device or is not allowed, or loops that must not
+ * pay for one.  ibf_projection_plan allocates its workspace; this entry point takes
+ * the same workspace from one fixed device array of IBF_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  It never calls
+ * cudaMalloc/cudaFree or any allocating routine.
+ *
+ * Projects one grid like ibf_project (same layouts, conventions, precisions and
+ * results; no statistics).  `in` and `out` are single ibf_fields of DEVICE pointers
+ * (out may alias in); stream is a cudaStream_t or NULL.  The pivot table is rebuilt
+ * on every call.  Every call shares the one array and leaves its contents behind, so
+ * calls that overlap on the GPU (other streams, other host threads) race and corrupt
+ * each other: order them.  The first call on a device looks up the array's device
+ * address and caches it; make that first call before any stream capture.
+ * Errors: INVALID_ARG, UNSUPPORTED_BC, UNSUPPORTED_SIZE (also when the workspace
+ * of the grid does not fit in IBF_NOALLOC_SCRATCH_BYTES: about 2.5 million cells in
+ * IBF_MIXED, 4.5 million in IBF_FP64), CUDA. */
+#define IBF_NOALLOC_SCRATCH_BYTES (64ull << 20)
+ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *opts, const ibf_fields *in,
+                               const ibf_fields *out, double dt, double alpha, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ IBF_MAX_GRIDS = 4096
 # every entry point declared in include/ibf.h
 EXPORTS = ("ibf_projection_plan", "ibf_project", "ibf_project_backward", "ibf_plan_sync_status",
            "ibf_plan_destroy", "ibf_status_string", "ibf_last_error", "ibf_plan_get_info",
-           "ibf_profile_enable", "ibf_profile_read", "ibf_profile_reset")
+           "ibf_profile_enable", "ibf_profile_read", "ibf_profile_reset", "ibf_project_noalloc")
 
 
 class ibf_grid(C.Structure):
@@ -99,6 +99,9 @@ def lib():
         L.ibf_profile_read.restype = C.c_int
         L.ibf_profile_reset.argtypes = [vp]
         L.ibf_profile_reset.restype = C.c_int
+        L.ibf_project_noalloc.argtypes = [C.POINTER(ibf_grid), C.POINTER(ibf_opts), C.POINTER(ibf_fields),
+                                          C.POINTER(ibf_fields), C.c_double, C.c_double, vp]
+        L.ibf_project_noalloc.restype = C.c_int
         _lib = L
     return _lib
 

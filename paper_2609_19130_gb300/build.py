@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["ibf_kernels.cu", "ibf_capi.cpp"]
+SOURCES = ["ibf_kernels.cu", "ibf_capi.cpp", "ibf_noalloc.cu"]
 HEADERS = ["ibf_device.cuh", "ibf_internal.h", "tw96.inc"]
 
 
