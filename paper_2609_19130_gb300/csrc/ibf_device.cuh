@@ -107,27 +107,34 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 // df32 -> fp64 without fp64 arithmetic.  For a normalised pair (|lo| <= ulp(hi),
 // which every df_* operation returns) hi + lo is exactly an fp64 number in hi's
 // binade, so it is hi's fp64 bit pattern plus lo's significand aligned to hi's fp64
-// ulp; the only binade change possible is a borrow below a power of two (hi's
-// fraction zero, lo of opposite sign), where the ulp halves.  lo bits below
-// 2^-52 of hi are truncated.
+// ulp (at most 2^29, so 32-bit arithmetic suffices); the only binade change
+// possible is a borrow below a power of two (hi's fraction zero, lo of opposite
+// sign), where the ulp halves.  lo bits below 2^-52 of hi are truncated.
 __device__ __forceinline__ double df_to_f64(df a) {
     const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
-    const unsigned eh = (hb >> 23) & 0xFFu, el = (lb >> 23) & 0xFFu;
-    if (eh == 0u) return f32_to_f64(a.lo);  // hi zero or subnormal: lo carries the value
-    unsigned long long H = __double_as_longlong(f32_to_f64(a.hi));
-    if (eh == 0xFFu || el == 0u) return __longlong_as_double((long long)H);
-    const unsigned long long L = (unsigned long long)((1u << 23) | (lb & 0x7FFFFFu));
-    const int sh = (int)el - (int)eh + 29;
-    unsigned long long Li = 0ull;
-    if (sh >= 0) Li = L << sh;
-    else if (sh > -25) Li = L >> (-sh);
-    if ((hb ^ lb) & 0x80000000u) {
-        if ((hb & 0x7FFFFFu) == 0u) Li <<= 1;
-        H -= Li;
-    } else {
-        H += Li;
+    const unsigned ha = hb & 0x7FFFFFFFu;
+    if (ha == 0u) return f32_to_f64(a.lo);                  // hi zero: lo carries the value
+    // hi as fp64: sign, exponent + 896, fraction << 29 (hi normal and finite)
+    unsigned hw = (hb & 0x80000000u) | ((ha >> 3) + 0x38000000u);
+    unsigned lw = hb << 29;
+    if (ha < 0x00800000u || ha >= 0x7F800000u) return f32_to_f64(a.hi);  // subnormal / inf / nan
+    const unsigned el = (lb >> 23) & 0xFFu;
+    if (el != 0u) {
+        const unsigned L = (1u << 23) | (lb & 0x7FFFFFu);
+        const int sh = (int)el - (int)(ha >> 23) + 29;           // <= 5 for a normalised pair
+        unsigned Li = 0u;
+        if (sh >= 0) Li = L << min(sh, 8);
+        else if (sh > -24) Li = L >> (-sh);
+        unsigned long long H = ((unsigned long long)hw << 32) | lw;
+        if ((hb ^ lb) & 0x80000000u) {
+            if ((ha & 0x7FFFFFu) == 0u) Li <<= 1;
+            H -= Li;
+        } else {
+            H += Li;
+        }
+        return __longlong_as_double((long long)H);
     }
-    return __longlong_as_double((long long)H);
+    return __longlong_as_double((long long)(((unsigned long long)hw << 32) | lw));
 }
 
 // ------------------------------------------------------------------ precision policies

@@ -833,15 +833,17 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
                 V Pim = shup(Pc, 1);
                 if (own_dn) Pim = ped[q];
                 if (act) {
+                    // the correction t is formed in the solve's high precision; the face
+                    // value u* + t is one fp64 add (the fp64 pipe is otherwise idle here)
                     const int c = row + i;
-                    uo[c] = A::store(A::add(A::load(ru[q]), A::mul(cu, A::sub(Pim, Pc))));
-                    vo[c] = A::store(A::add(A::load(rv[q]), A::mul(cv, A::sub(Pjm, Pc))));
+                    uo[c] = ru[q] + A::store(A::mul(cu, A::sub(Pim, Pc)));
+                    vo[c] = rv[q] + A::store(A::mul(cv, A::sub(Pjm, Pc)));
                     if (ADJ) {
-                        wo[c] = A::store(A::add(A::load(rw[q]), A::sub(pkm[q], Pc)));
-                        if (k == nz - 1) wo[c + plane] = A::store(A::add(A::load(rwt[q]), Pc));
+                        wo[c] = rw[q] + A::store(A::sub(pkm[q], Pc));
+                        if (k == nz - 1) wo[c + plane] = rwt[q] + A::store(A::norm(Pc));
                     } else {
                         if (k == 0) wo[c] = rw[q];
-                        else wo[c] = A::store(A::add(A::load(rw[q]), A::mul(cw, A::sub(pkm[q], Pc))));
+                        else wo[c] = rw[q] + A::store(A::mul(cw, A::sub(pkm[q], Pc)));
                         if (k == nz - 1) wo[c + plane] = rwt[q];
                         if (po) po[c] = A::store(A::norm(Pc));
                     }
