@@ -16,16 +16,24 @@
  * tridiagonal system along z per horizontal mode.  Everything runs on one GPU
  * in hand-written sm_103a kernels; there is no CPU fallback.
  *
+ * Beyond the paper (which has x and y periodic), x and/or y may also be
+ * wall-bounded (IBF_BC_NEUMANN): that direction then uses a DCT-II, computed
+ * with an FFT of the same length between a reordering and pre/post twiddles
+ * (Makhoul 1980), instead of the real FFT.
+ *
  * Discretisation fixed by this library (the paper states only "staggered,
  * second-order centred"):
  *   cells i < nx, j < ny, k < nz;  dx = lx/nx, dy = ly/ny;
  *   z faces zf[0..nz] with zf[0] = 0, zf[nz] = lz;  hz_k = zf[k+1]-zf[k];
  *   cell centres zc_k = (zf_k + zf_{k+1})/2;  gz_k = zc_k - zc_{k-1};
- *   u[k][j][i] on the x-face x = i dx (left face of cell i), shape [nz][ny][nx];
- *   v[k][j][i] on the y-face y = j dy, shape [nz][ny][nx];
+ *   u[k][j][i] on the x-face x = i dx (left face of cell i), shape [nz][ny][nx],
+ *     or [nz][ny][nx+1] when x is wall-bounded (faces 0 and nx are the walls);
+ *   v[k][j][i] on the y-face y = j dy, shape [nz][ny][nx], or [nz][ny+1][nx] when y
+ *     is wall-bounded (rows 0 and ny are the walls);
  *   w[k][j][i] on the z-face z = zf[k], shape [nz+1][ny][nx] (k = 0, nz: walls);
  *   p (phi)   at cell centres, shape [nz][ny][nx];  all float64, i fastest.
- *   (D u)_c = (u_{i+1}-u_i)/dx + (v_{j+1}-v_j)/dy + (w_{k+1}-w_k)/hz_k (periodic wrap);
+ *   (D u)_c = (u_{i+1}-u_i)/dx + (v_{j+1}-v_j)/dy + (w_{k+1}-w_k)/hz_k (wrap in a
+ *   periodic direction);
  *   G phi on interior faces (difference over dx, dy or gz_k), zero on the walls,
  *   so the wall-normal velocity is left unchanged.
  *   Reference value: the volume-weighted mean of the right-hand side is removed
@@ -55,7 +63,8 @@ typedef enum ibf_status {
     IBF_ERR_TIMEOUT = 5,          /* a bounded device wait gave up (reported by ibf_plan_sync_status) */
     IBF_ERR_NONFINITE = 6,        /* NaN or Inf met in the right-hand side (ibf_plan_sync_status) */
     IBF_WARN_INCOMPATIBLE_RHS = 7,/* |compatibility defect| above 1e-8 of the RHS scale; result still returned */
-    IBF_ERR_UNSUPPORTED_BC = 8    /* a boundary condition this build does not implement */
+    IBF_ERR_UNSUPPORTED_BC = 8    /* a boundary condition this build does not implement
+                                     (Dirichlet; walls in x or y for ibf_project_noalloc) */
 } ibf_status;
 
 typedef enum ibf_bc {
@@ -78,7 +87,7 @@ typedef struct ibf_grid {
                                zf[nz] = lz, or NULL to use the tanh map below */
     double beta;            /* tanh clustering factor when zf == NULL:
                                zf_k = lz/2 (1 + tanh(beta (2k/nz - 1)) / tanh(beta)); beta = 0: uniform */
-    int bc_x, bc_y;         /* ibf_bc; this build: IBF_BC_PERIODIC */
+    int bc_x, bc_y;         /* ibf_bc: IBF_BC_PERIODIC, or IBF_BC_NEUMANN (walls, DCT-II) */
     int bc_zlo, bc_zhi;     /* ibf_bc; this build: IBF_BC_NEUMANN */
 } ibf_grid;
 

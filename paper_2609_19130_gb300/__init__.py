@@ -27,7 +27,8 @@ class Grid:
     """One staggered grid (cells nx x ny x nz on [0,lx] x [0,ly] x [0,lz]).
 
     z faces: explicit ascending `zf` (nz+1 values, zf[0]=0, zf[nz]=lz), or the tanh
-    map with clustering factor `beta` (0: uniform)."""
+    map with clustering factor `beta` (0: uniform).  x and y are periodic by default;
+    bc_x / bc_y = IBF_BC_NEUMANN makes that direction wall-bounded (DCT-II transform)."""
     nx: int
     ny: int
     nz: int
@@ -43,7 +44,10 @@ class Grid:
 
     @property
     def shapes(self):
-        return ((self.nz, self.ny, self.nx), (self.nz, self.ny, self.nx), (self.nz + 1, self.ny, self.nx))
+        """(u, v, w) shapes; a wall-bounded x (y) direction adds the far wall face to u (v)."""
+        nxu = self.nx + (self.bc_x == N.IBF_BC_NEUMANN)
+        nyv = self.ny + (self.bc_y == N.IBF_BC_NEUMANN)
+        return ((self.nz, self.ny, nxu), (self.nz, nyv, self.nx), (self.nz + 1, self.ny, self.nx))
 
     @property
     def cells(self):
@@ -157,7 +161,7 @@ class Plan:
                 o = out[g]
             else:
                 o = (torch.empty_like(f[0]), torch.empty_like(f[1]), torch.empty_like(f[2]),
-                     torch.empty(su, dtype=torch.float64, device=f[0].device))
+                     torch.empty((grid.nz, grid.ny, grid.nx), dtype=torch.float64, device=f[0].device))
             outs.append(o)
         st = None
         if stats:

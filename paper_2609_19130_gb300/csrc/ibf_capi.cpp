@@ -128,7 +128,7 @@ ibf_status validate(const ibf_grid *g, std::vector<double> &zf) {
     const int bcs[4] = {g->bc_x, g->bc_y, g->bc_zlo, g->bc_zhi};
     for (int b : bcs)
         if (b < IBF_BC_PERIODIC || b > IBF_BC_DIRICHLET) return IBF_ERR_INVALID_ARG;
-    if (g->bc_x != IBF_BC_PERIODIC || g->bc_y != IBF_BC_PERIODIC) return IBF_ERR_UNSUPPORTED_BC;
+    if (g->bc_x == IBF_BC_DIRICHLET || g->bc_y == IBF_BC_DIRICHLET) return IBF_ERR_UNSUPPORTED_BC;
     if (g->bc_zlo != IBF_BC_NEUMANN || g->bc_zhi != IBF_BC_NEUMANN) return IBF_ERR_UNSUPPORTED_BC;
     int a, b;
     if (!factor(g->nx, &a, &b) || !factor(g->ny, &a, &b)) return IBF_ERR_UNSUPPORTED_SIZE;
@@ -176,6 +176,19 @@ void twiddles(int n, std::vector<double> &out) {
     }
 }
 
+// exp(-i pi m / (2n)), m < n: the DCT-II post-twiddles (Makhoul)
+void dct_twiddles(int n, std::vector<double> &out) {
+    out.resize(2 * (size_t)n);
+    for (int m = 0; m < n; ++m) {
+        const double a = M_PI * (double)m / (2.0 * (double)n);
+        out[2 * m] = std::cos(a);
+        out[2 * m + 1] = -std::sin(a);
+    }
+}
+
+// x-modes kept by the x transform: nx/2 + 1 (real FFT) or nx (DCT-II, wall-bounded x)
+int x_modes(const ibf_grid &g) { return g.bc_x == IBF_BC_NEUMANN ? g.nx : g.nx / 2 + 1; }
+
 ibf_status upload(const void *host, void *dev, size_t bytes) {
     cudaError_t e = cudaMemcpy(dev, host, bytes, cudaMemcpyHostToDevice);
     return e == cudaSuccess ? IBF_OK : cuda_fail(e, "cudaMemcpy");
@@ -194,7 +207,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
 
     pl->grids.resize(ngrids);
     long long total_cols = 0;
-    for (int g = 0; g < ngrids; ++g) total_cols += grids[g].nx / 2 + 1;
+    for (int g = 0; g < ngrids; ++g) total_cols += x_modes(grids[g]);
 
     long long spec = 0, cells = 0;
     int zoff = 0, poff = 0, xblk = 0, yzblk = 0;
@@ -208,7 +221,11 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
         GridDev &d = H.d;
         memset(&d, 0, sizeof(d));
         d.nx = H.g.nx; d.ny = H.g.ny; d.nz = H.g.nz;
-        d.nxh = d.nx / 2 + 1;
+        d.nxh = x_modes(H.g);
+        d.wall_x = H.g.bc_x == IBF_BC_NEUMANN;
+        d.wall_y = H.g.bc_y == IBF_BC_NEUMANN;
+        d.nxu = d.nx + d.wall_x;
+        d.nyv = d.ny + d.wall_y;
         factor(d.nx, &d.nx1, &d.nx2);
         factor(d.ny, &d.ny1, &d.ny2);
         // y-FFT + tridiagonal column blocks: at most 4096 modes per CTA (shared-memory state),
@@ -242,6 +259,16 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
         d.twy_off = (int)(twy_all.size() / 2);
         twiddles(d.ny, tmp);
         twy_all.insert(twy_all.end(), tmp.begin(), tmp.end());
+        d.dctx_off = (int)(twx_all.size() / 2);
+        if (d.wall_x) {
+            dct_twiddles(d.nx, tmp);
+            twx_all.insert(twx_all.end(), tmp.begin(), tmp.end());
+        }
+        d.dcty_off = (int)(twy_all.size() / 2);
+        if (d.wall_y) {
+            dct_twiddles(d.ny, tmp);
+            twy_all.insert(twy_all.end(), tmp.begin(), tmp.end());
+        }
         d.xblk_off = xblk;
         xblk += d.nz * d.nrb;
         d.yzblk_off = yzblk;
@@ -316,6 +343,8 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
     // device allocations
     Work &w = pl->work;
     w.ngrids = ngrids;
+    w.walls = 0;
+    for (int g = 0; g < ngrids; ++g) w.walls |= pl->grids[g].d.wall_x | pl->grids[g].d.wall_y;
     GridDev *dgrids;
     IBF_TRY(dalloc(pl, &dgrids, sizeof(GridDev) * ngrids));
     w.grids = dgrids;

@@ -1,0 +1,156 @@
+// ibf_common.cuh -- device helpers shared by the x-direction kernels (ibf_kernels.cu)
+// and the y/z-direction kernels (ibf_yz.cu): grid lookup of batched launches,
+// precision-policy traits, fixed-order block reductions, warp shuffles, phi sources
+// and the row-segment mapping of the x kernels.
+#pragma once
+#include "ibf_device.cuh"
+#include "ibf_internal.h"
+
+namespace ibf {
+
+__device__ __forceinline__ int find_grid(const int *start, int n, int b) {
+    int lo = 0, hi = n;  // start[lo] <= b < start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(start + mid) <= b) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <class A> struct IsDF { static constexpr bool value = false; };
+template <> struct IsDF<DFArith> { static constexpr bool value = true; };
+
+template <class A> struct Coef;
+template <> struct Coef<F64Arith> {
+    __device__ __forceinline__ static double c(double x) { return x; }
+    __device__ __forceinline__ static double c2(float2 v, double x) { return x; }
+};
+template <> struct Coef<DFArith> {
+    __device__ __forceinline__ static df c(double x) { return f64_to_df(x); }
+    __device__ __forceinline__ static df c2(float2 v, double) { return {v.x, v.y}; }
+};
+
+template <class A> __device__ __forceinline__ float absv(typename A::V v);
+template <> __device__ __forceinline__ float absv<F64Arith>(double v) { return fabsf((float)v); }
+template <> __device__ __forceinline__ float absv<DFArith>(df v) { return fabsf(v.hi); }
+
+template <typename T, class A> __device__ __forceinline__ T to_T(typename A::V v);
+template <> __device__ __forceinline__ double to_T<double, F64Arith>(double v) { return v; }
+template <> __device__ __forceinline__ float to_T<float, DFArith>(df v) { return df_to_f(v); }
+
+// DCT-II through an N-point FFT (Makhoul, IEEE TASSP 28(1), 1980): sample i goes to
+// FFT input position i/2 (i even) or N - (i+1)/2 (i odd); the inverse un-reorders the
+// same way.  Coefficient m is Re(exp(-i pi m/(2N)) V_m) of the FFT V of the reordered
+// sequence.
+__device__ __forceinline__ int dct_perm(int i, int n) { return (i & 1) ? n - ((i + 1) >> 1) : (i >> 1); }
+
+// ---------------------------------------------------------------- block reductions (fixed order)
+template <class A> struct Red;
+template <> struct Red<F64Arith> {
+    __device__ static double sum(double v, double *sh) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        if (lane == 0) sh[wid] = v;
+        __syncthreads();
+        double r = 0.0;
+        if (threadIdx.x == 0)
+            for (int i = 0; i < nw; ++i) r += sh[i];
+        __syncthreads();
+        return r;  // valid in thread 0
+    }
+};
+template <> struct Red<DFArith> {
+    __device__ static df sum(df v, double *sh) {
+        for (int o = 16; o > 0; o >>= 1) {
+            df u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+            v = df_add(v, u);
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        float2 *s2 = reinterpret_cast<float2 *>(sh);
+        if (lane == 0) s2[wid] = make_float2(v.hi, v.lo);
+        __syncthreads();
+        df r = df_make(0.f);
+        if (threadIdx.x == 0)
+            for (int i = 0; i < nw; ++i) r = df_add(r, df{s2[i].x, s2[i].y});
+        __syncthreads();
+        return r;
+    }
+};
+
+__device__ __forceinline__ float block_max(float v, float *sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    float r = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) r = fmaxf(r, sh[i]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v) {
+    // non-negative doubles (and NaN, whose pattern is larger) order like their bit patterns
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------- warp helpers
+template <class V> __device__ __forceinline__ V shdown(V v, int d);
+template <> __device__ __forceinline__ df shdown<df>(df v, int d) {
+    return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+template <> __device__ __forceinline__ double shdown<double>(double v, int d) {
+    return __shfl_down_sync(0xffffffffu, v, d);
+}
+template <class V> __device__ __forceinline__ V shup(V v, int d);
+template <> __device__ __forceinline__ df shup<df>(df v, int d) {
+    return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+template <> __device__ __forceinline__ double shup<double>(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+
+// phi of the solve being refined: float-float (hi, lo) arrays on the mixed path
+// (lo absent before the first accumulation), fp64 array on the fp64 path.
+template <class A> struct PhiSrc;
+template <> struct PhiSrc<DFArith> {
+    const float *hi, *lo;
+    __device__ __forceinline__ df get(ptrdiff_t o) const { return {__ldg(hi + o), lo ? __ldg(lo + o) : 0.f}; }
+};
+template <> struct PhiSrc<F64Arith> {
+    const double *p;
+    __device__ __forceinline__ double get(ptrdiff_t o) const { return __ldg(p + o); }
+};
+
+// Cells of a CTA's (plane, rows) block are visited by warps in 32-wide row
+// segments: lanes hold consecutive i (x-neighbours by shuffle), and each warp
+// walks its rows upward (y-neighbours carried in registers).  With fewer segments
+// than warps the rows are split into chunks.
+struct SegMap {
+    int seg0, segstep, nseg, r0, r1;
+};
+__device__ __forceinline__ SegMap seg_map(int nx, int rows) {
+    const int warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    SegMap m;
+    m.nseg = (nx + 31) >> 5;
+    if (m.nseg >= NW) {
+        m.seg0 = warp; m.segstep = NW; m.r0 = 0; m.r1 = rows;
+    } else {
+        const int nchunk = NW / m.nseg;
+        const int chunk = warp / m.nseg;
+        m.seg0 = warp - chunk * m.nseg;
+        m.segstep = m.nseg;
+        if (chunk >= nchunk) {
+            m.seg0 = m.nseg; m.r0 = 0; m.r1 = 0;
+        } else {
+            const int rpc = (rows + nchunk - 1) / nchunk;
+            m.r0 = min(rows, chunk * rpc);
+            m.r1 = min(rows, m.r0 + rpc);
+        }
+    }
+    return m;
+}
+
+
+// one-dimensional launch grid
+static inline dim3 grid1(int n) { return dim3((unsigned)n); }
+
+}  // namespace ibf

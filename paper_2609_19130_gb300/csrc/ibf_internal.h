@@ -21,7 +21,10 @@ struct FDiv {
 
 // Per-grid descriptor, one entry per grid in device memory.
 struct GridDev {
-    int nx, ny, nz, nxh;       // cells; nxh = nx/2 + 1 x-modes kept by the real transform
+    int nx, ny, nz, nxh;       // cells; x-modes kept: nx/2 + 1 (real FFT) or nx (DCT-II)
+    int wall_x, wall_y;        // 1: that direction is wall-bounded (Neumann phi, DCT-II transform)
+    int nxu, nyv;              // faces of u per row (nx + wall_x), rows of v per plane (ny + wall_y)
+    int dctx_off, dcty_off;    // offsets of the exp(-i pi m/(2N)) tables of the DCTs (in twx / twy)
     int nx1, nx2, ny1, ny2;    // two-level FFT factors: nx = nx1*nx2, ny = ny1*ny2
     int mb, ncb;               // x-modes per column block of the yz kernels, number of blocks
     int rows, nrb;             // rows per CTA of the x kernels (even), row blocks per plane
@@ -53,6 +56,7 @@ struct ZArrays {
 struct Work {
     const GridDev *grids;      // [ngrids]
     int ngrids;
+    int walls;                 // some grid has a wall-bounded x or y (selects the kernels that handle it)
     const int *xblk_start;     // prefix of x-kernel blocks over grids [ngrids+1]
     const int *yzblk_start;    // prefix of yz-kernel blocks over grids [ngrids+1]
     ZArrays z;
@@ -96,5 +100,7 @@ cudaError_t launch_finalize(const Work &w, double *max_div, double *max_div_in, 
                             cudaStream_t st);
 cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t st);
 cudaError_t set_smem_limits(int mixed);
+cudaError_t set_smem_limits_yz(int mixed);  // the y/z kernels' share of set_smem_limits
+cudaError_t set_smem_cap(const void *fn);   // one kernel's dynamic shared-memory cap
 
 }  // namespace ibf

@@ -24,152 +24,19 @@
 // Two precisions: fp64 (T = double, F64Arith) and mixed (T = float transforms and
 // sweeps, DFArith float-float stencils / residual / accumulation, fp64 I/O converted
 // with integer bit operations).
-#include "ibf_device.cuh"
-#include "ibf_internal.h"
+#include "ibf_common.cuh"
+
+#include <type_traits>
 
 namespace ibf {
-
-__device__ __forceinline__ int find_grid(const int *start, int n, int b) {
-    int lo = 0, hi = n;  // start[lo] <= b < start[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(start + mid) <= b) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-template <class A> struct IsDF { static constexpr bool value = false; };
-template <> struct IsDF<DFArith> { static constexpr bool value = true; };
-
-template <class A> struct Coef;
-template <> struct Coef<F64Arith> {
-    __device__ __forceinline__ static double c(double x) { return x; }
-    __device__ __forceinline__ static double c2(float2 v, double x) { return x; }
-};
-template <> struct Coef<DFArith> {
-    __device__ __forceinline__ static df c(double x) { return f64_to_df(x); }
-    __device__ __forceinline__ static df c2(float2 v, double) { return {v.x, v.y}; }
-};
-
-template <class A> __device__ __forceinline__ float absv(typename A::V v);
-template <> __device__ __forceinline__ float absv<F64Arith>(double v) { return fabsf((float)v); }
-template <> __device__ __forceinline__ float absv<DFArith>(df v) { return fabsf(v.hi); }
-
-template <typename T, class A> __device__ __forceinline__ T to_T(typename A::V v);
-template <> __device__ __forceinline__ double to_T<double, F64Arith>(double v) { return v; }
-template <> __device__ __forceinline__ float to_T<float, DFArith>(df v) { return df_to_f(v); }
-
-// ---------------------------------------------------------------- block reductions (fixed order)
-template <class A> struct Red;
-template <> struct Red<F64Arith> {
-    __device__ static double sum(double v, double *sh) {
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        if (lane == 0) sh[wid] = v;
-        __syncthreads();
-        double r = 0.0;
-        if (threadIdx.x == 0)
-            for (int i = 0; i < nw; ++i) r += sh[i];
-        __syncthreads();
-        return r;  // valid in thread 0
-    }
-};
-template <> struct Red<DFArith> {
-    __device__ static df sum(df v, double *sh) {
-        for (int o = 16; o > 0; o >>= 1) {
-            df u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
-            v = df_add(v, u);
-        }
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        float2 *s2 = reinterpret_cast<float2 *>(sh);
-        if (lane == 0) s2[wid] = make_float2(v.hi, v.lo);
-        __syncthreads();
-        df r = df_make(0.f);
-        if (threadIdx.x == 0)
-            for (int i = 0; i < nw; ++i) r = df_add(r, df{s2[i].x, s2[i].y});
-        __syncthreads();
-        return r;
-    }
-};
-
-__device__ __forceinline__ float block_max(float v, float *sh) {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    float r = 0.f;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < nw; ++i) r = fmaxf(r, sh[i]);
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v) {
-    // non-negative doubles (and NaN, whose pattern is larger) order like their bit patterns
-    atomicMax(p, (unsigned long long)__double_as_longlong(v));
-}
-
-// ---------------------------------------------------------------- warp helpers
-template <class V> __device__ __forceinline__ V shdown(V v, int d);
-template <> __device__ __forceinline__ df shdown<df>(df v, int d) {
-    return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
-}
-template <> __device__ __forceinline__ double shdown<double>(double v, int d) {
-    return __shfl_down_sync(0xffffffffu, v, d);
-}
-template <class V> __device__ __forceinline__ V shup(V v, int d);
-template <> __device__ __forceinline__ df shup<df>(df v, int d) {
-    return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
-}
-template <> __device__ __forceinline__ double shup<double>(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
-
-// phi of the solve being refined: float-float (hi, lo) arrays on the mixed path
-// (lo absent before the first accumulation), fp64 array on the fp64 path.
-template <class A> struct PhiSrc;
-template <> struct PhiSrc<DFArith> {
-    const float *hi, *lo;
-    __device__ __forceinline__ df get(ptrdiff_t o) const { return {__ldg(hi + o), lo ? __ldg(lo + o) : 0.f}; }
-};
-template <> struct PhiSrc<F64Arith> {
-    const double *p;
-    __device__ __forceinline__ double get(ptrdiff_t o) const { return __ldg(p + o); }
-};
-
-// Cells of a CTA's (plane, rows) block are visited by warps in 32-wide row
-// segments: lanes hold consecutive i (x-neighbours by shuffle), and each warp
-// walks its rows upward (y-neighbours carried in registers).  With fewer segments
-// than warps the rows are split into chunks.
-struct SegMap {
-    int seg0, segstep, nseg, r0, r1;
-};
-__device__ __forceinline__ SegMap seg_map(int nx, int rows) {
-    const int warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
-    SegMap m;
-    m.nseg = (nx + 31) >> 5;
-    if (m.nseg >= NW) {
-        m.seg0 = warp; m.segstep = NW; m.r0 = 0; m.r1 = rows;
-    } else {
-        const int nchunk = NW / m.nseg;
-        const int chunk = warp / m.nseg;
-        m.seg0 = warp - chunk * m.nseg;
-        m.segstep = m.nseg;
-        if (chunk >= nchunk) {
-            m.seg0 = m.nseg; m.r0 = 0; m.r1 = 0;
-        } else {
-            const int rpc = (rows + nchunk - 1) / nchunk;
-            m.r0 = min(rows, chunk * rpc);
-            m.r1 = min(rows, m.r0 + rpc);
-        }
-    }
-    return m;
-}
 
 // ================================================================ k_xfwd
 constexpr int kRowGroup = 4;  // rows whose loads are issued together (memory-level parallelism)
 
 // Right-hand side of one solve for a block of rows of plane k, then the real FFT
 // along x of the rows (two rows per complex transform), stored as x-modes.
-template <typename T, class A, int MODE>
+// W: the launch contains wall-bounded grids (compiled out of periodic-only plans).
+template <typename T, class A, int MODE, bool W>
 __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     k_xfwd(Work w, UserPtrs p, int use_ws, int lo_valid, double s, double rs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -192,6 +59,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const int zo = G.z_off;
     const ptrdiff_t plane = (ptrdiff_t)nx * ny;
     const ptrdiff_t pbase = (ptrdiff_t)k * plane;
+    const int wall_x = W ? G.wall_x : 0, wall_y = W ? G.wall_y : 0, nxu = W ? G.nxu : nx;
 
     V cu, cv, cwp, cwm, cp;
     if (MODE == XM_DIV) {
@@ -227,13 +95,20 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
         const int i = seg * 32 + lane;
         const bool act = i < nx;
         const int ii = act ? i : nx - 1;  // inactive lanes load a valid cell and discard it
-        const int ip = (ii + 1 == nx) ? 0 : ii + 1;
+        // right neighbour: the next face of the u row (face nx when x is wall-bounded) on
+        // the divergence paths, the next cell (periodic wrap) on the residual path
+        const int ip = (ii + 1 == nx && (MODE == XM_RESID || !wall_x)) ? 0 : ii + 1;
         const int im = (ii == 0) ? nx - 1 : ii - 1;
         const bool own_up = (lane == 31) || (ii + 1 == nx);
         const bool own_dn = (lane == 0) || (ii == 0);
-        const int spos = pos_nat(ii, fN2);
+        const int spos = pos_nat(wall_x ? dct_perm(ii, nx) : ii, fN2);
         if (MODE == XM_DIV || MODE == XM_ADJ) {
-            const double *u = p.in_u[gi] + pbase, *vv = p.in_v[gi] + pbase, *ww = p.in_w[gi] + pbase;
+            // wall-bounded x: u rows hold nx+1 faces; wall-bounded y: v planes hold ny+1 rows
+            const double *u = p.in_u[gi] + (ptrdiff_t)k * ny * nxu;
+            const double *vv = p.in_v[gi] + (ptrdiff_t)k * (W ? G.nyv : ny) * nx, *ww = p.in_w[gi] + pbase;
+            // adjoint source: G^T skips wall faces (G is zero there)
+            const bool zero_u = MODE == XM_ADJ && wall_x && ii == 0;
+            const bool zero_un = MODE == XM_ADJ && wall_x && ii + 1 == nx;
             const double *pp = (MODE == XM_ADJ && p.in_p[gi]) ? p.in_p[gi] + pbase : nullptr;
             V vcur = A::zero();
             bool have_v = false;
@@ -248,10 +123,10 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                     const int jl = jg + q, j = j0 + jl;
                     ru[q] = rue[q] = rvn[q] = rw0[q] = rw1[q] = rp[q] = 0.0;
                     if (jl < sm.r1 && j < ny) {
-                        const int jp = (j + 1 == ny) ? 0 : j + 1;
-                        const int row = j * nx;
-                        ru[q] = __ldg(u + row + ii);
-                        if (own_up) rue[q] = __ldg(u + row + ip);
+                        const int jp = (j + 1 == ny && !wall_y) ? 0 : j + 1;
+                        const int row = j * nx, rowu = j * nxu;
+                        ru[q] = __ldg(u + rowu + ii);
+                        if (own_up) rue[q] = __ldg(u + rowu + ip);
                         if (q == 0 && need_v0) rv0 = __ldg(vv + row + ii);
                         rvn[q] = __ldg(vv + jp * nx + ii);
                         rw0[q] = __ldg(ww + row + ii);
@@ -267,19 +142,26 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                     T val = (T)0;
                     if (j < ny) {
                         const int row = j * nx;
-                        const V U = A::load(ru[q]);
+                        V U = A::load(ru[q]);
                         V Un = shdown(U, 1);
                         if (own_up) Un = A::load(rue[q]);
-                        const V Vn = A::load(rvn[q]);
+                        V Vn = A::load(rvn[q]);
                         const V W0 = A::load(rw0[q]), W1 = A::load(rw1[q]);
-                        V bv = A::add(A::mul(cu, A::sub(Un, U)), A::mul(cv, A::sub(Vn, vcur)));
+                        V Vc = vcur;
+                        vcur = Vn;
+                        if (MODE == XM_ADJ) {
+                            if (zero_u) U = A::zero();
+                            if (zero_un) Un = A::zero();
+                            if (wall_y && j == 0) Vc = A::zero();
+                            if (wall_y && j + 1 == ny) Vn = A::zero();
+                        }
+                        V bv = A::add(A::mul(cu, A::sub(Un, U)), A::mul(cv, A::sub(Vn, Vc)));
                         if (MODE == XM_DIV) {
                             bv = A::add(bv, A::mul(cwp, A::sub(W1, W0)));
                         } else {
                             bv = A::add(bv, A::sub(A::mul(cwp, W1), A::mul(cwm, W0)));
                             if (pp) bv = A::add(bv, A::mul(cp, A::load(rp[q])));
                         }
-                        vcur = Vn;
                         have_v = true;
                         if (act) {
                             if (MODE == XM_DIV) vmax = fmaxf(vmax, absv<A>(bv));
@@ -345,8 +227,11 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                         if (own_dn) Pim = ped[q];
                         const V dzp = (k + 1 < nz) ? A::sub(pkp[q], Pc) : A::zero();
                         const V dzm = (k > 0) ? A::sub(Pc, pkm[q]) : A::zero();
-                        const V dxp = A::sub(Pip, Pc), dxm = A::sub(Pc, Pim);
-                        const V dyp = A::sub(pn[q], Pc), dym = A::sub(Pc, Pm);
+                        // wall faces carry no gradient (Neumann phi)
+                        const V dxp = (wall_x && ii + 1 == nx) ? A::zero() : A::sub(Pip, Pc);
+                        const V dxm = (wall_x && ii == 0) ? A::zero() : A::sub(Pc, Pim);
+                        const V dyp = (wall_y && j + 1 == ny) ? A::zero() : A::sub(pn[q], Pc);
+                        const V dym = (wall_y && j == 0) ? A::zero() : A::sub(Pc, Pm);
                         V lap = A::add(A::mul(cu, A::sub(dxp, dxm)), A::mul(cv, A::sub(dyp, dym)));
                         lap = A::add(lap, A::sub(A::mul(cwp, dzp), A::mul(cwm, dzm)));
                         if (act) {
@@ -402,278 +287,19 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
         cx<T> X;
         if ((jl & 1) == 0) X = {(Zm.x + Zc.x) * (T)0.5, (Zm.y - Zc.y) * (T)0.5};
         else X = {(Zm.y + Zc.y) * (T)0.5, (Zc.x - Zm.x) * (T)0.5};
+        if (wall_x) {  // DCT-II coefficient m = Re(exp(-i pi m/(2 nx)) X_m), kept as (c, 0)
+            const cx<T> tw = twx[G.dctx_off - G.twx_off + m];
+            X = {tw.x * X.x - tw.y * X.y, (T)0};
+        }
         spec[((size_t)cb * ny + j) * mb + mm] = X;
     }
-}
-
-// ================================================================ k_yzfwd / k_yzbwd
-template <typename T> __device__ __forceinline__ const T *zarr(const double *d, const float *f);
-template <> __device__ __forceinline__ const double *zarr<double>(const double *d, const float *) { return d; }
-template <> __device__ __forceinline__ const float *zarr<float>(const double *, const float *f) { return f; }
-
-// cp.async (sm_80+ asynchronous global->shared copy, L1-bypassing for 16 B) of one element
-template <int BYTES> __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem_src), "n"(BYTES));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-// y-FFT + Thomas forward elimination of one column block, sweeping k = 0..nz-1.
-// Shared memory: kYZStages x [FFT buffer (mb padded sequences) | pivot chunk], then the
-// Thomas state d'_{k-1} of every mode of the block.  Plane k+1 (spectrum and pivots)
-// is copied with cp.async while plane k is transformed and eliminated.
-template <typename T>
-__global__ void __launch_bounds__(kYZThreads) k_yzfwd(Work w) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = find_grid(w.yzblk_start, w.ngrids, blockIdx.x);
-    const GridDev &G = w.grids[g];
-    const int cb = blockIdx.x - __ldg(w.yzblk_start + g);
-    const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
-    const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
-    const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
-    const int nslot = ny * mb;
-    const int nvalid = min(mb, nxh - cb * mb);  // valid x-modes of this block
-    const cx<T> *twy = reinterpret_cast<const cx<T> *>(w.twy) + G.twy_off;
-    const T *az = zarr<T>(w.z.az, w.z.azf) + G.z_off;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const size_t fftsz = (size_t)mb * sstride;  // complex elements of one FFT buffer
-    const size_t stage_bytes = ((fftsz * sizeof(cx<T>) + (size_t)nslot * sizeof(T)) + 15) & ~(size_t)15;
-    auto fbuf = [&](int st) { return reinterpret_cast<cx<T> *>(smem_raw + st * stage_bytes); };
-    auto tbuf = [&](int st) { return reinterpret_cast<T *>(smem_raw + st * stage_bytes + fftsz * sizeof(cx<T>)); };
-    cx<T> *state = reinterpret_cast<cx<T> *>(smem_raw + kYZStages * stage_bytes);
-    const cx<T> *spec = reinterpret_cast<const cx<T> *>(w.spec) + G.spec_off;
-    cx<T> *specw = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
-    const T *tab = reinterpret_cast<const T *>(w.tab) + G.tab_off;
-
-    auto issue = [&](int k) {
-        if (k < nz) {
-            const int st = k % kYZStages;
-            cx<T> *fb = fbuf(st);
-            T *tb = tbuf(st);
-            const cx<T> *src = spec + ((size_t)k * ncb + cb) * nslot;
-            const T *tsrc = tab + ((size_t)k * ncb + cb) * nslot;
-            for (int t = tid; t < nslot; t += nthr) {
-                const int j = (int)fdiv((unsigned)t, fmb), mm = t - j * mb;
-                cx<T> *dst = fb + mm * sstride + pos_nat(j, fN2);
-                if (mm < nvalid) cp_async<sizeof(cx<T>)>(dst, src + t);
-                else *dst = {(T)0, (T)0};
-                cp_async<sizeof(T)>(tb + t, tsrc + t);
-            }
-        }
-        cp_async_commit();
-    };
-
-    for (int q = tid; q < nslot; q += nthr) state[q] = {(T)0, (T)0};
-    for (int k = 0; k < kYZStages - 1; ++k) issue(k);
-
-    for (int k = 0; k < nz; ++k) {
-        issue(k + kYZStages - 1);
-        cp_async_wait<kYZStages - 1>();
-        __syncthreads();
-        cx<T> *buf = fbuf(k % kYZStages);
-        const T *tb = tbuf(k % kYZStages);
-        fft_batch<T, -1>(buf, mb, sstride, N1, N2, fN1, fN2, twy);
-        cx<T> *pl = specw + ((size_t)k * ncb + cb) * nslot;
-        const T a = az[k];
-        for (int q = tid; q < nslot; q += nthr) {
-            const int sn = (int)fdiv((unsigned)q, fmb), mm = q - sn * mb;
-            const cx<T> rin = buf[mm * sstride + pos_nat(sn, fN2)];
-            const T inv = tb[q];
-            const cx<T> dp = state[q];
-            cx<T> d = {(rin.x - a * dp.x) * inv, (rin.y - a * dp.y) * inv};
-            if (cb == 0 && q == 0) d = rin;  // (0,0) mode: solved by k_00
-            state[q] = d;
-            if (mm < nvalid) pl[q] = d;
-        }
-        __syncthreads();
-    }
-    cp_async_wait<0>();
-}
-
-// Back substitution and inverse y-FFT of one column block, sweeping k = nz-1..0.
-// Shared memory: kYZStages x [d' chunk (slot order) | pivot chunk], then one FFT
-// buffer and the state phi_hat_{k+1}; plane k-1 is copied while plane k is processed.
-template <typename T>
-__global__ void __launch_bounds__(kYZThreads) k_yzbwd(Work w) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = find_grid(w.yzblk_start, w.ngrids, blockIdx.x);
-    const GridDev &G = w.grids[g];
-    const int cb = blockIdx.x - __ldg(w.yzblk_start + g);
-    const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
-    const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
-    const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
-    const int nslot = ny * mb;
-    const int nvalid = min(mb, nxh - cb * mb);
-    const cx<T> *twy = reinterpret_cast<const cx<T> *>(w.twy) + G.twy_off;
-    const T *cz = zarr<T>(w.z.cz, w.z.czf) + G.z_off;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const size_t stage_bytes = (((size_t)nslot * (sizeof(cx<T>) + sizeof(T))) + 15) & ~(size_t)15;
-    auto dbuf = [&](int st) { return reinterpret_cast<cx<T> *>(smem_raw + st * stage_bytes); };
-    auto tbuf = [&](int st) { return reinterpret_cast<T *>(smem_raw + st * stage_bytes + (size_t)nslot * sizeof(cx<T>)); };
-    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw + kYZStages * stage_bytes);
-    cx<T> *state = buf + (size_t)mb * sstride;
-    cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
-    const T *tab = reinterpret_cast<const T *>(w.tab) + G.tab_off;
-
-    auto issue = [&](int k) {  // plane k (k >= 0) into stage (nz-1-k) % S
-        if (k >= 0) {
-            const int st = (nz - 1 - k) % kYZStages;
-            cx<T> *db = dbuf(st);
-            T *tb = tbuf(st);
-            const cx<T> *src = spec + ((size_t)k * ncb + cb) * nslot;
-            const T *tsrc = tab + ((size_t)k * ncb + cb) * nslot;
-            for (int t = tid; t < nslot; t += nthr) {
-                const int sn = (int)fdiv((unsigned)t, fmb), mm = t - sn * mb;
-                if (mm < nvalid) cp_async<sizeof(cx<T>)>(db + t, src + t);
-                else db[t] = {(T)0, (T)0};
-                cp_async<sizeof(T)>(tb + t, tsrc + t);
-            }
-        }
-        cp_async_commit();
-    };
-
-    for (int q = tid; q < nslot; q += nthr) state[q] = {(T)0, (T)0};
-    for (int s_ = 0; s_ < kYZStages - 1; ++s_) issue(nz - 1 - s_);
-
-    for (int k = nz - 1; k >= 0; --k) {
-        issue(k - (kYZStages - 1));
-        cp_async_wait<kYZStages - 1>();
-        __syncthreads();
-        const int st = (nz - 1 - k) % kYZStages;
-        const cx<T> *db = dbuf(st);
-        const T *tb = tbuf(st);
-        const T c = cz[k];
-        for (int q = tid; q < nslot; q += nthr) {
-            const int sn = (int)fdiv((unsigned)q, fmb), mm = q - sn * mb;
-            const cx<T> d = db[q];
-            const T cp = c * tb[q];
-            const cx<T> nx_ = state[q];
-            cx<T> ph = {d.x - cp * nx_.x, d.y - cp * nx_.y};
-            if (cb == 0 && q == 0) ph = d;
-            state[q] = ph;
-            buf[mm * sstride + pos_nat(sn, fN2)] = ph;
-        }
-        __syncthreads();
-        fft_batch<T, +1>(buf, mb, sstride, N1, N2, fN1, fN2, twy);
-        cx<T> *pl = spec + ((size_t)k * ncb + cb) * nslot;
-        for (int t = tid; t < nslot; t += nthr) {
-            const int j = (int)fdiv((unsigned)t, fmb), mm = t - j * mb;
-            if (mm < nvalid) pl[t] = buf[mm * sstride + pos_nat(j, fN2)];
-        }
-        __syncthreads();
-    }
-    cp_async_wait<0>();
-}
-
-// ================================================================ k_00 (fp64, one CTA per grid)
-template <typename T>
-__global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
-    // Shared memory: right-hand side, hz, and two copies (ping-pong) of the four PCR
-    // arrays a, b, c, d; every array has nz+1 entries.
-    extern __shared__ double sh00[];
-    __shared__ double red[8];
-    const int g = blockIdx.x;
-    const GridDev &G = w.grids[g];
-    const int nz = G.nz, nrb = G.nrb, zo = G.z_off;
-    const int L = nz + 1;
-    double *rhs = sh00, *hz = sh00 + L;
-    double *A0 = sh00 + 2 * L, *B0 = A0 + L, *C0 = B0 + L, *D0 = C0 + L;
-    double *A1 = D0 + L, *B1 = A1 + L, *C1 = B1 + L, *D1 = C1 + L;
-    const double *part = w.partial + G.part_off;
-    double loc = 0.0, locp = 0.0;
-    bool bad = false;
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        double S = 0.0;
-        for (int r = 0; r < nrb; ++r) S += part[k * nrb + r];
-        const double m = S * G.inv_nxy;  // plane mean of the right-hand side
-        if (!isfinite(m)) bad = true;
-        const double h = w.z.hz[zo + k];
-        rhs[k] = m;
-        hz[k] = h;
-        loc += h * m;
-        if (!first_solve) {
-            double P = 0.0;
-            for (int r = 0; r < nrb; ++r) P += w.partial_phi[G.part_off + k * nrb + r];
-            locp += h * P * G.inv_nxy;
-        }
-    }
-    if (bad) atomicOr(w.err, 1u << 6);  // IBF_ERR_NONFINITE
-    __syncthreads();
-    const double tot = Red<F64Arith>::sum(loc, red);
-    // weighted mean of the phi being refined: the correction also removes it, so that
-    // phi + delta keeps a zero weighted mean (L cannot see a constant)
-    const double totp = first_solve ? 0.0 : Red<F64Arith>::sum(locp, red);
-    if (threadIdx.x == 0) red[0] = tot / G.sum_hz;
-    __syncthreads();
-    const double mean = red[0];
-    if (threadIdx.x == 0 && first_solve) {
-        w.mean_b[g] = mean;
-        double scale = 0.0;
-        for (int k = 0; k < nz; ++k) scale = fmax(scale, fabs(rhs[k]));
-        // compatibility defect large compared with the plane means -> warning
-        if (fabs(mean) > 1e-8 * scale && fabs(mean) > 0.0) atomicOr(w.err, 1u << 7);
-    }
-    // Pinned system (level 0 fixed to zero, so row 0 reads phi_0 = 0) solved by
-    // parallel cyclic reduction (Hockney 1965): each step eliminates from every row its
-    // couplings at distance st; after ceil(log2 nz) steps row k reads phi_k = d_k / b_k.
-    // Row k of L along z: a = az_k (to k-1), b = -(az_k + cz_k), c = cz_k (to k+1).
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        if (k == 0) { A0[k] = 0.0; B0[k] = 1.0; C0[k] = 0.0; D0[k] = 0.0; }
-        else {
-            const double a = w.z.az[zo + k], c = w.z.cz[zo + k];
-            A0[k] = a; B0[k] = -(a + c); C0[k] = (k == 0) ? 0.0 : c; D0[k] = rhs[k] - mean;
-        }
-    }
-    __syncthreads();
-    for (int st = 1; st < nz; st <<= 1) {
-        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-            double na = 0.0, nb = B0[k], nc = 0.0, nd = D0[k];
-            if (k - st >= 0) {
-                const double al = -A0[k] / B0[k - st];
-                na = al * A0[k - st];
-                nb += al * C0[k - st];
-                nd += al * D0[k - st];
-            }
-            if (k + st < nz) {
-                const double ga = -C0[k] / B0[k + st];
-                nc = ga * C0[k + st];
-                nb += ga * A0[k + st];
-                nd += ga * D0[k + st];
-            }
-            A1[k] = na; B1[k] = nb; C1[k] = nc; D1[k] = nd;
-        }
-        __syncthreads();
-        double *t;
-        t = A0; A0 = A1; A1 = t;
-        t = B0; B0 = B1; B1 = t;
-        t = C0; C0 = C1; C1 = t;
-        t = D0; D0 = D1; D1 = t;
-    }
-    double lsv = 0.0;
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        const double ph = D0[k] / B0[k];
-        rhs[k] = ph;
-        lsv += hz[k] * ph;
-    }
-    __syncthreads();
-    const double sv = Red<F64Arith>::sum(lsv, red);
-    if (threadIdx.x == 0) rhs[nz] = (sv + totp) / G.sum_hz;  // weighted mean to remove
-    __syncthreads();
-    const double mphi = rhs[nz];
-    cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
-    const size_t stride = (size_t)G.ncb * G.ny * G.mb;
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) spec[(size_t)k * stride] = {(T)(rhs[k] - mphi), (T)0};
 }
 
 // ================================================================ k_xinv
 // Inverse real FFT along x of a block of rows; STORE writes phi (fp64 path: fp64
 // array; mixed path: the hi array of the float-float phi), ACCUM adds the
 // refinement correction to the float-float phi.
-template <typename T, class A, int IMODE>
+template <typename T, class A, int IMODE, bool W>
 __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     k_xinv(Work w, UserPtrs p, int use_ws, int lo_valid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -690,6 +316,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const FDiv fN1 = G.fnx1, fN2 = G.fnx2, fmb = G.fmb, fnpair = G.fnpair, fnx = G.fnx;
     const int mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const cx<T> *spec = reinterpret_cast<const cx<T> *>(w.spec) + G.spec_off + (size_t)k * ncb * ny * mb;
+    const cx<T> *twx = reinterpret_cast<const cx<T> *>(w.twx) + G.twx_off;
     const int npair = rows >> 1;
     const int nload = ncb * npair * mb;
     for (int t = threadIdx.x; t < nload; t += blockDim.x) {
@@ -704,11 +331,26 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
         if (ja < ny) A_ = spec[((size_t)cb * ny + ja) * mb + mm];
         if (jb < ny) B_ = spec[((size_t)cb * ny + jb) * mb + mm];
         cx<T> *seq = buf + s_ * sstride;
+        if (W && G.wall_x) {
+            // DCT-III input stage of two real coefficient rows a, b (real parts of the
+            // spectrum): V_m = conj(W^m)(X_m - i X_{N-m}) per row, X_N = 0, packed as
+            // V^a + i V^b; the unscaled inverse FFT then yields row a + i row b, reordered.
+            T ac = (T)0, bc = (T)0;
+            if (m > 0) {
+                const int mc = nx - m, cbc = mc / mb, mmc = mc - cbc * mb;
+                if (ja < ny) ac = spec[((size_t)cbc * ny + ja) * mb + mmc].x;
+                if (jb < ny) bc = spec[((size_t)cbc * ny + jb) * mb + mmc].x;
+            }
+            const cx<T> tw = twx[G.dctx_off - G.twx_off + m];
+            const cx<T> Va = {tw.x * A_.x - tw.y * ac, -tw.x * ac - tw.y * A_.x};
+            const cx<T> Vb = {tw.x * B_.x - tw.y * bc, -tw.x * bc - tw.y * B_.x};
+            seq[pos_tr(m, N1, N2, fN1)] = {Va.x - Vb.y, Va.y + Vb.x};
+            continue;
+        }
         seq[pos_tr(m, N1, N2, fN1)] = {A_.x - B_.y, A_.y + B_.x};
         if (m > 0 && 2 * m < nx) seq[pos_tr(nx - m, N1, N2, fN1)] = {A_.x + B_.y, B_.x - A_.y};
     }
     __syncthreads();
-    const cx<T> *twx = reinterpret_cast<const cx<T> *>(w.twx) + G.twx_off;
     fft_batch<T, +1>(buf, npair, sstride, N1, N2, fN1, fN2, twx);
 
     const int gi = g - p.g0;
@@ -724,7 +366,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     }
     for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
         const int jl = (int)fdiv((unsigned)t, fnx), i = t - jl * nx;
-        const cx<T> z = buf[(jl >> 1) * sstride + pos_nat(i, fN2)];
+        const cx<T> z = buf[(jl >> 1) * sstride + pos_nat((W && G.wall_x) ? dct_perm(i, nx) : i, fN2)];
         const T val = (jl & 1) ? z.y : z.x;
         if constexpr (sizeof(T) == 8) {
             phi64[t] = (double)val;
@@ -751,7 +393,7 @@ constexpr int kRowGroupC = 2;
 //                    mixed path: also writes phi (fp64) from its float-float value.
 // adjoint (ADJ = 1): g* = g_u + hz_k rdx (psi_{i-1} - psi_i), ...,
 //                    w_k = g_w,k + psi_{k-1} [k>=1] - psi_k [k<=nz-1].
-template <class A, int ADJ>
+template <class A, int ADJ, bool W>
 __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, int use_ws, int lo_valid, double s) {
     typedef typename A::V V;
     const int b = blockIdx.x + p.blk0;
@@ -774,8 +416,11 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
     } else {
         ph.p = (use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi]) + pbase;
     }
-    const double *ui = p.in_u[gi] + pbase, *vi = p.in_v[gi] + pbase, *wi = p.in_w[gi] + pbase;
-    double *uo = p.out_u[gi] + pbase, *vo = p.out_v[gi] + pbase, *wo = p.out_w[gi] + pbase;
+    // wall-bounded x: u rows hold nx+1 faces; wall-bounded y: v planes hold ny+1 rows
+    const int wall_x = W ? G.wall_x : 0, wall_y = W ? G.wall_y : 0, nxu = W ? G.nxu : nx;
+    const ptrdiff_t ubase = (ptrdiff_t)k * ny * nxu, vbase = (ptrdiff_t)k * (W ? G.nyv : ny) * nx;
+    const double *ui = p.in_u[gi] + ubase, *vi = p.in_v[gi] + vbase, *wi = p.in_w[gi] + pbase;
+    double *uo = p.out_u[gi] + ubase, *vo = p.out_v[gi] + vbase, *wo = p.out_w[gi] + pbase;
     double *po = (MIX && !ADJ) ? p.out_p[gi] + pbase : nullptr;
     V cu, cv, cw;
     if (ADJ) {
@@ -796,6 +441,7 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
         const int ii = act ? i : nx - 1;
         const int im = (ii == 0) ? nx - 1 : ii - 1;
         const bool own_dn = (lane == 0) || (ii == 0);
+        const bool wall_lo = wall_x && ii == 0;  // face 0 of a wall-bounded row
         V Pjm = A::zero();
         bool have = false;
         for (int jg = sm.r0; jg < sm.r1; jg += kRowGroupC) {
@@ -816,7 +462,7 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
                     if (k > 0) pkm[q] = ph.get(row + ii - plane);
                     if (own_dn) ped[q] = ph.get(row + im);
                     if (act) {
-                        ru[q] = ui[row + i];
+                        ru[q] = ui[j * nxu + i];
                         rv[q] = vi[row + i];
                         rw[q] = wi[row + i];
                         if (k == nz - 1) rwt[q] = wi[row + i + plane];
@@ -832,12 +478,16 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
                 const V Pc = pc[q];
                 V Pim = shup(Pc, 1);
                 if (own_dn) Pim = ped[q];
+                // wall faces: no gradient (forward: velocity copied); the adjoint's D^T
+                // there sees only the one interior cell
+                if (wall_lo) Pim = ADJ ? A::zero() : Pc;
+                const V Pjw = (wall_y && j == 0) ? (ADJ ? A::zero() : Pc) : Pjm;
                 if (act) {
                     // the correction t is formed in the solve's high precision; the face
                     // value u* + t is one fp64 add (the fp64 pipe is otherwise idle here)
                     const int c = row + i;
-                    uo[c] = ru[q] + A::store(A::mul(cu, A::sub(Pim, Pc)));
-                    vo[c] = rv[q] + A::store(A::mul(cv, A::sub(Pjm, Pc)));
+                    uo[j * nxu + i] = ru[q] + A::store(A::mul(cu, A::sub(Pim, Pc)));
+                    vo[c] = rv[q] + A::store(A::mul(cv, A::sub(Pjw, Pc)));
                     if (ADJ) {
                         wo[c] = rw[q] + A::store(A::sub(pkm[q], Pc));
                         if (k == nz - 1) wo[c + plane] = rwt[q] + A::store(A::norm(Pc));
@@ -853,10 +503,24 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
             }
         }
     }
+    // the far wall faces: u face nx of every row (wall-bounded x), v row ny (wall-bounded y)
+    if (wall_x) {
+        const int nr = min(rows, ny - j0);
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+            const int j = j0 + t, f = j * nxu + nx;
+            uo[f] = ADJ ? ui[f] + A::store(A::mul(cu, ph.get(j * nx + nx - 1))) : ui[f];
+        }
+    }
+    if (wall_y && j0 + rows >= ny) {
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int f = ny * nx + i;
+            vo[f] = ADJ ? vi[f] + A::store(A::mul(cv, ph.get((ny - 1) * nx + i))) : vi[f];
+        }
+    }
 }
 
 // ================================================================ k_divstat: max |D u| of the output
-template <class A>
+template <class A, bool W>
 __global__ void __launch_bounds__(kXThreads) k_divstat(Work w, UserPtrs p) {
     typedef typename A::V V;
     __shared__ float redf[kXThreads / 32];
@@ -871,17 +535,19 @@ __global__ void __launch_bounds__(kXThreads) k_divstat(Work w, UserPtrs p) {
     const int gi = g - p.g0;
     const ptrdiff_t plane = (ptrdiff_t)nx * ny;
     const ptrdiff_t pbase = (ptrdiff_t)k * plane;
-    const double *u = p.out_u[gi] + pbase, *vv = p.out_v[gi] + pbase, *ww = p.out_w[gi] + pbase;
+    const int wall_x = W ? G.wall_x : 0, wall_y = W ? G.wall_y : 0, nxu = W ? G.nxu : nx;
+    const double *u = p.out_u[gi] + (ptrdiff_t)k * ny * nxu, *vv = p.out_v[gi] + (ptrdiff_t)k * (W ? G.nyv : ny) * nx,
+                 *ww = p.out_w[gi] + pbase;
     const V cu = Coef<A>::c(G.rdx), cv = Coef<A>::c(G.rdy), cw = Coef<A>::c(w.z.rhz[G.z_off + k]);
     float mx = 0.f;
     const int ncell = min(rows, ny - j0) * nx;
     for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
         const int jl = (int)fdiv((unsigned)t, G.fnx), i = t - jl * nx;
         const int j = j0 + jl;
-        const int ip = (i + 1 == nx) ? 0 : i + 1;
-        const int jp = (j + 1 == ny) ? 0 : j + 1;
-        const int row = j * nx;
-        V d = A::mul(cu, A::sub(A::load(u[row + ip]), A::load(u[row + i])));
+        const int ip = (i + 1 == nx && !wall_x) ? 0 : i + 1;
+        const int jp = (j + 1 == ny && !wall_y) ? 0 : j + 1;
+        const int row = j * nx, rowu = j * nxu;
+        V d = A::mul(cu, A::sub(A::load(u[rowu + ip]), A::load(u[rowu + i])));
         d = A::add(d, A::mul(cv, A::sub(A::load(vv[jp * nx + i]), A::load(vv[row + i]))));
         d = A::add(d, A::mul(cw, A::sub(A::load(ww[plane + row + i]), A::load(ww[row + i]))));
         const float a = absv<A>(d);
@@ -900,91 +566,67 @@ __global__ void k_finalize(Work w, double *max_div, double *max_div_in, double *
     if (compat) compat[g] = w.mean_b[g];
 }
 
-// Pivots of every mode's tridiagonal system (fp64 arithmetic, stored as T):
-// inv_k = 1/(bz_k + lambda - az_k c'_{k-1}),  c'_k = cz_k inv_k,  bz_k = -(az_k + cz_k),
-// lambda = -4/dx^2 sin^2(pi m/nx) - 4/dy^2 sin^2(pi n/ny).
-template <typename T>
-__global__ void __launch_bounds__(256) k_build_table(Work w) {
-    const int g = find_grid(w.yzblk_start, w.ngrids, blockIdx.x);
-    const GridDev &G = w.grids[g];
-    const int cb = blockIdx.x - w.yzblk_start[g];
-    const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb;
-    const int N1 = G.ny1, N2 = G.ny2;
-    const int nslot = ny * mb;
-    const double *az = w.z.az + G.z_off, *cz = w.z.cz + G.z_off;
-    T *tab = reinterpret_cast<T *>(w.tab) + G.tab_off;
-    for (int q = threadIdx.x; q < nslot; q += blockDim.x) {
-        const int mm = q % mb, sn = q / mb;
-        const int n = (sn / N2) + N1 * (sn % N2);
-        const int m = cb * mb + mm;
-        const bool valid = (m < G.nxh) && !(m == 0 && n == 0);
-        const double sx = sinpi((double)m / G.nx), sy = sinpi((double)n / ny);
-        const double lam = -4.0 * G.rdx * G.rdx * sx * sx - 4.0 * G.rdy * G.rdy * sy * sy;
-        double cp = 0.0;
-        for (int k = 0; k < nz; ++k) {
-            double inv = 0.0;
-            if (valid) {
-                inv = 1.0 / (-(az[k] + cz[k]) + lam - az[k] * cp);
-                cp = cz[k] * inv;
-            }
-            tab[((size_t)k * ncb + cb) * nslot + q] = (T)inv;
-        }
-    }
-}
 
 // ================================================================ launchers
-static inline dim3 grid1(int n) { return dim3((unsigned)n); }
 
-cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
-                        double s, double rs, size_t smem, cudaStream_t st) {
-    if (nblk <= 0) return cudaSuccess;
+template <bool W>
+cudaError_t launch_xfwd_w(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
+                          double s, double rs, size_t smem, cudaStream_t st) {
     if (mixed) {
         if (mode == XM_DIV)
-            k_xfwd<float, DFArith, XM_DIV><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+            k_xfwd<float, DFArith, XM_DIV, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else if (mode == XM_RESID)
-            k_xfwd<float, DFArith, XM_RESID><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+            k_xfwd<float, DFArith, XM_RESID, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else
-            k_xfwd<float, DFArith, XM_ADJ><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+            k_xfwd<float, DFArith, XM_ADJ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
     } else {
         if (mode == XM_DIV)
-            k_xfwd<double, F64Arith, XM_DIV><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+            k_xfwd<double, F64Arith, XM_DIV, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else if (mode == XM_ADJ)
-            k_xfwd<double, F64Arith, XM_ADJ><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+            k_xfwd<double, F64Arith, XM_ADJ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else
             return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_yzfwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st) {
-    if (mixed) k_yzfwd<float><<<grid1(nblk), kYZThreads, smem, st>>>(w);
-    else k_yzfwd<double><<<grid1(nblk), kYZThreads, smem, st>>>(w);
-    return cudaGetLastError();
+cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
+                        double s, double rs, size_t smem, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    return w.walls ? launch_xfwd_w<true>(mixed, mode, w, p, use_ws, lo_valid, nblk, s, rs, smem, st)
+                   : launch_xfwd_w<false>(mixed, mode, w, p, use_ws, lo_valid, nblk, s, rs, smem, st);
 }
 
-cudaError_t launch_yzbwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st) {
-    if (mixed) k_yzbwd<float><<<grid1(nblk), kYZThreads, smem, st>>>(w);
-    else k_yzbwd<double><<<grid1(nblk), kYZThreads, smem, st>>>(w);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cudaStream_t st) {
-    const size_t smem = (size_t)10 * (maxnz + 1) * sizeof(double);
-    if (mixed) k_00<float><<<w.ngrids, 256, smem, st>>>(w, first_solve);
-    else k_00<double><<<w.ngrids, 256, smem, st>>>(w, first_solve);
+template <bool W>
+cudaError_t launch_xinv_w(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
+                          size_t smem, cudaStream_t st) {
+    if (mixed) {
+        if (mode == IM_STORE)
+            k_xinv<float, DFArith, IM_STORE, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+        else
+            k_xinv<float, DFArith, IM_ACCUM, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+    } else {
+        k_xinv<double, F64Arith, IM_STORE, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
                         size_t smem, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
+    return w.walls ? launch_xinv_w<true>(mixed, mode, w, p, use_ws, lo_valid, nblk, smem, st)
+                   : launch_xinv_w<false>(mixed, mode, w, p, use_ws, lo_valid, nblk, smem, st);
+}
+
+template <bool W>
+cudaError_t launch_correct_w(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
+                             int nblk, double s, cudaStream_t st) {
     if (mixed) {
-        if (mode == IM_STORE)
-            k_xinv<float, DFArith, IM_STORE><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
-        else
-            k_xinv<float, DFArith, IM_ACCUM><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+        if (adjoint) k_correct<DFArith, 1, W><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
+        else k_correct<DFArith, 0, W><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
     } else {
-        k_xinv<double, F64Arith, IM_STORE><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+        if (adjoint) k_correct<F64Arith, 1, W><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
+        else k_correct<F64Arith, 0, W><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
     }
     return cudaGetLastError();
 }
@@ -992,20 +634,19 @@ cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, i
 cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
                            int nblk, double s, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
-    if (mixed) {
-        if (adjoint) k_correct<DFArith, 1><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
-        else k_correct<DFArith, 0><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
-    } else {
-        if (adjoint) k_correct<F64Arith, 1><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
-        else k_correct<F64Arith, 0><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
-    }
-    return cudaGetLastError();
+    return w.walls ? launch_correct_w<true>(mixed, adjoint, w, p, use_ws, lo_valid, nblk, s, st)
+                   : launch_correct_w<false>(mixed, adjoint, w, p, use_ws, lo_valid, nblk, s, st);
 }
 
 cudaError_t launch_divstat(int mixed, const Work &w, const UserPtrs &p, int nblk, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
-    if (mixed) k_divstat<DFArith><<<grid1(nblk), kXThreads, 0, st>>>(w, p);
-    else k_divstat<F64Arith><<<grid1(nblk), kXThreads, 0, st>>>(w, p);
+    if (mixed) {
+        if (w.walls) k_divstat<DFArith, true><<<grid1(nblk), kXThreads, 0, st>>>(w, p);
+        else k_divstat<DFArith, false><<<grid1(nblk), kXThreads, 0, st>>>(w, p);
+    } else {
+        if (w.walls) k_divstat<F64Arith, true><<<grid1(nblk), kXThreads, 0, st>>>(w, p);
+        else k_divstat<F64Arith, false><<<grid1(nblk), kXThreads, 0, st>>>(w, p);
+    }
     return cudaGetLastError();
 }
 
@@ -1015,43 +656,42 @@ cudaError_t launch_finalize(const Work &w, double *max_div, double *max_div_in, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t st) {
-    if (mixed) k_build_table<float><<<grid1(nblk), 256, 0, st>>>(w);
-    else k_build_table<double><<<grid1(nblk), 256, 0, st>>>(w);
-    return cudaGetLastError();
-}
-
 // Dynamic shared-memory caps are per-kernel attributes shared by every plan in the
 // process: each is set to the device's opt-in maximum minus the kernel's static shared
 // memory, so that no plan can lower them under another plan's launch size.
-cudaError_t set_smem_limits(int mixed) {
+cudaError_t set_smem_cap(const void *fn) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes a;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, fn);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+    return e;
+}
+
+cudaError_t set_smem_limits(int mixed) {
+    cudaError_t e = cudaSuccess;
     auto set = [&](const void *fn) {
-        if (e != cudaSuccess) return;
-        cudaFuncAttributes a;
-        e = cudaFuncGetAttributes(&a, fn);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+        if (e == cudaSuccess) e = set_smem_cap(fn);
     };
-    if (mixed) {
-        set((const void *)k_xfwd<float, DFArith, XM_DIV>);
-        set((const void *)k_xfwd<float, DFArith, XM_RESID>);
-        set((const void *)k_xfwd<float, DFArith, XM_ADJ>);
-        set((const void *)k_xinv<float, DFArith, IM_STORE>);
-        set((const void *)k_xinv<float, DFArith, IM_ACCUM>);
-        set((const void *)k_yzfwd<float>);
-        set((const void *)k_yzbwd<float>);
-        set((const void *)k_00<float>);
-    } else {
-        set((const void *)k_xfwd<double, F64Arith, XM_DIV>);
-        set((const void *)k_xfwd<double, F64Arith, XM_ADJ>);
-        set((const void *)k_xinv<double, F64Arith, IM_STORE>);
-        set((const void *)k_yzfwd<double>);
-        set((const void *)k_yzbwd<double>);
-        set((const void *)k_00<double>);
-    }
+    auto set_all = [&](auto wtag) {
+        constexpr bool W = decltype(wtag)::value;
+        if (mixed) {
+            set((const void *)k_xfwd<float, DFArith, XM_DIV, W>);
+            set((const void *)k_xfwd<float, DFArith, XM_RESID, W>);
+            set((const void *)k_xfwd<float, DFArith, XM_ADJ, W>);
+            set((const void *)k_xinv<float, DFArith, IM_STORE, W>);
+            set((const void *)k_xinv<float, DFArith, IM_ACCUM, W>);
+        } else {
+            set((const void *)k_xfwd<double, F64Arith, XM_DIV, W>);
+            set((const void *)k_xfwd<double, F64Arith, XM_ADJ, W>);
+            set((const void *)k_xinv<double, F64Arith, IM_STORE, W>);
+        }
+    };
+    set_all(std::false_type{});
+    set_all(std::true_type{});
+    if (e == cudaSuccess) e = set_smem_limits_yz(mixed);
     return e;
 }
 

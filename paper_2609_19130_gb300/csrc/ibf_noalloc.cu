@@ -140,6 +140,8 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     // launch shapes: the rules of ibf_projection_plan for a one-grid plan
     d.nx = g.nx; d.ny = g.ny; d.nz = nz;
     d.nxh = d.nx / 2 + 1;
+    d.nxu = d.nx;  // periodic x and y only: no wall faces
+    d.nyv = d.ny;
     const int mbmax = std::max(1, std::min(d.nxh, 4096 / d.ny));
     const int want = (64 + d.ny2 - 1) / d.ny2;
     d.mb = std::min(std::min(mbmax, want), std::max(1, d.nxh / nsm));

@@ -61,7 +61,9 @@ def _plan(grid_kw, opts_kw=None, n=1):
     (dict(nx=5), N.IBF_ERR_UNSUPPORTED_SIZE),       # prime 5
     (dict(ny=2048), N.IBF_ERR_UNSUPPORTED_SIZE),    # > 32*32
     (dict(nx=27), N.IBF_ERR_UNSUPPORTED_SIZE),      # 27 = 3*9, 9 not a register size
-    (dict(bc_x=1), N.IBF_ERR_UNSUPPORTED_BC),
+    (dict(bc_x=2), N.IBF_ERR_UNSUPPORTED_BC),       # Dirichlet x
+    (dict(bc_y=2), N.IBF_ERR_UNSUPPORTED_BC),       # Dirichlet y
+    (dict(bc_x=1, nx=5), N.IBF_ERR_UNSUPPORTED_SIZE),  # wall-bounded x: same FFT sizes
     (dict(bc_zhi=2), N.IBF_ERR_UNSUPPORTED_BC),
     (dict(bc_zlo=7), N.IBF_ERR_INVALID_ARG),
     (dict(beta=-1.0), N.IBF_ERR_INVALID_ARG),
