@@ -41,6 +41,21 @@ BYTES_MIXED = {"x_forward_div": 36.0, "yz_forward": 10.0, "yz_backward": 10.0, "
                "x_forward_residual": 16.0, "x_inverse_accumulate": 16.0, "correct": 64.0, "mode00": 0.0}
 BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x_inverse_store": 16.0,
               "correct": 56.0, "mode00": 0.0}
+# DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of each
+# kernel from one ncu capture (512x512x128 mixed, see profiles/), valid while the
+# kernel sources hash to SOURCES_SHA256; otherwise the roofline's traffic is null.
+NCU_TRAFFIC_B_PER_CELL = {}
+NCU_SOURCES_SHA256 = None
+KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_common.cuh", "ibf_device.cuh", "ibf_internal.h")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2609_19130_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def peaks():
@@ -235,10 +250,12 @@ def main():
     ap.add_argument("--size", default="1024x1024x512")
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--ref-nz", type=int, default=4, help="z levels of the oracle sample per reference step")
-    ap.add_argument("--cpu-nz", type=int, default=8, help="z levels of the cpu_baseline sample")
+    ap.add_argument("--cpu-nz", type=int, default=16, help="z levels of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--autotune", type=int, default=0, help="1: plan-time autotuning of the launch shapes")
+    ap.add_argument("--tuning", default="", help="JSON dict of ibf_tuning fields forced for the mixed plan")
     ap.add_argument("--cpu-child", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_child:
@@ -269,7 +286,9 @@ def main():
     res = {}
     clocks = None
     for prec in ([MIXED] + ([] if args.no_fp64 else [FP64])):
-        plan = Plan([g], precision=prec, refine_steps=args.refine if prec == MIXED else 0, device=dev.index)
+        tun = [json.loads(args.tuning)] if (args.tuning and prec == MIXED) else None
+        plan = Plan([g], precision=prec, refine_steps=args.refine if prec == MIXED else 0, device=dev.index,
+                    autotune=bool(args.autotune), tuning=tun)
         if prec == MIXED:
             with Clocks(dev.index) as ck:
                 ms, prof = time_steps(plan, ins, outs, args.steps, args.warmup, ws)
@@ -282,7 +301,7 @@ def main():
         else:
             ms, prof = time_steps(plan, ins, outs, args.steps, args.warmup, ws)
             diag = None
-        res[prec] = {"ms": ms, "prof": prof, "diag": diag, "plan": plan}
+        res[prec] = {"ms": ms, "prof": prof, "diag": diag, "plan": plan, "tuning": plan.tuning(0)}
 
     mixed = res[MIXED]
     ms = mixed["ms"]
@@ -295,6 +314,9 @@ def main():
     per_launch_ms = dms / dcount
     per_launch_bytes = BYTES_MIXED.get(dname, 0.0) * cells
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = None
+    if dname in NCU_TRAFFIC_B_PER_CELL and NCU_SOURCES_SHA256 == kernel_sources_sha256():
+        traffic = NCU_TRAFFIC_B_PER_CELL[dname] * cells
     bytes_model = sum(BYTES_MIXED[k] * c / args.steps for k, (c, _) in prof.items() if k in BYTES_MIXED)
     kernels = {k: {"launches": c, "ms_per_launch": t / c, "share": t / sum(x[1] for x in prof.values()),
                    "gbs_algorithmic": (BYTES_MIXED.get(k, 0.0) * cells / (t / c * 1e-3) / 1e9)}
@@ -309,9 +331,10 @@ def main():
                                f"mixed precision (fp32 transforms/sweeps, float-float stencils, fp64 I/O), "
                                f"{args.refine} refinement sweep(s)",
                    "grid": [nx, ny, nz], "refine_steps": args.refine, "parallelism": "replicas" if ws > 1 else "1 GPU",
+                   "launch_shape": mixed["tuning"], "autotuned": bool(args.autotune),
                    "l2_policy": "inputs 4.3 GB per field (> 129 MB L2): no flush between steps"},
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                      "bytes_per_cell": BYTES_MIXED.get(dname, 0.0)},
         "projection_hbm": {"bytes_per_cell_model": bytes_model,
                            "achieved_gbs": bytes_model * cells / (ms * 1e-3) / 1e9,

@@ -94,7 +94,9 @@ typedef struct ibf_grid {
 typedef struct ibf_opts {
     int precision;          /* ibf_precision */
     int refine_steps;       /* IBF_MIXED only: iterative-refinement sweeps after the first solve (0..8) */
-    int autotune;           /* 1: time candidate launch shapes at plan time (uses scratch, synchronises) */
+    int autotune;           /* 1: time candidate launch shapes (ibf_tuning) at plan time, once per
+                               distinct grid shape and precision in the process (allocates
+                               temporary device buffers, synchronises the device) */
     int reserved;           /* must be 0 */
 } ibf_opts;
 
@@ -142,6 +144,35 @@ ibf_status ibf_project(ibf_plan *plan, const ibf_fields *in, const ibf_fields *o
  * stream/capture rules as ibf_project. */
 ibf_status ibf_project_backward(ibf_plan *plan, const ibf_fields *grad_out, const ibf_fields *grad_in,
                                 double dt, double alpha, void *stream);
+
+/* Launch shape of one grid, chosen by ibf_projection_plan (defaults or, with
+ * opts->autotune, the fastest candidate timed on this device), or forced by the
+ * caller through ibf_projection_plan_tuned.  Every field <= 0 means "default".
+ *   rows      : grid rows per CTA of the x-direction kernels (even);
+ *   x_n1, y_n1: first factor of the two-level FFT along x / y (N = n1 * n2, both
+ *               factors in {1,2,3,4,6,8,12,16,24,32});
+ *   yz_kernel : 1 streaming y/z kernels (y-FFT fused with Thomas sweeps that stream
+ *               the planes, the spectrum read and written twice), 2 resident slab
+ *               (the whole z extent of a column block in shared memory: one read,
+ *               one write; small grids only);
+ *   mb        : x-modes per column block of the y/z kernels;
+ *   tri       : tridiagonal algorithm of the slab kernel: 1 Thomas per mode with the
+ *               plan's pivot table, 1 + S (S >= 1) S levels of in-place cyclic
+ *               reduction (all levels in parallel over modes and equations) before
+ *               Thomas on the reduced systems; 1 + log2(nz) is full cyclic reduction. */
+typedef struct ibf_tuning {
+    int rows, x_n1, y_n1, yz_kernel, mb, tri;
+} ibf_tuning;
+
+/* ibf_projection_plan with the launch shape of every grid given (tuning: ngrids
+ * entries, NULL = defaults; opts->autotune then only fills the fields left <= 0).
+ * Errors as ibf_projection_plan; UNSUPPORTED_SIZE when a forced shape does not fit
+ * the device (shared memory) or does not divide the grid. */
+ibf_status ibf_projection_plan_tuned(ibf_plan **plan, const ibf_grid *grids, int ngrids,
+                                     const ibf_opts *opts, int device, const ibf_tuning *tuning);
+
+/* The launch shape grid g of the plan uses (all fields filled). */
+ibf_status ibf_plan_get_tuning(const ibf_plan *plan, int g, ibf_tuning *out);
 
 /* Synchronise the plan's last stream, return and clear the device error word
  * (IBF_OK, IBF_ERR_TIMEOUT, IBF_ERR_NONFINITE or IBF_WARN_INCOMPATIBLE_RHS). */

@@ -79,7 +79,9 @@ class Plan:
     """A projection plan for a batch of grids on one device (owns its workspace)."""
 
     def __init__(self, grids, precision: str = MIXED, refine_steps: int = 1, device: int | None = None,
-                 autotune: bool = False):
+                 autotune: bool = False, tuning=None):
+        """tuning: None, or one dict per grid with any of the ibf_tuning fields (rows,
+        x_n1, y_n1, yz_kernel, mb, tri) to force; the rest default (or are autotuned)."""
         if isinstance(grids, Grid):
             grids = [grids]
         self.grids = list(grids)
@@ -100,7 +102,17 @@ class Plan:
             arr[i] = N.ibf_grid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, zf, g.beta, g.bc_x, g.bc_y, g.bc_zlo, g.bc_zhi)
         opts = N.ibf_opts(N.IBF_MIXED if precision == MIXED else N.IBF_FP64, self.refine_steps, int(autotune), 0)
         h = C.c_void_p()
-        st = N.lib().ibf_projection_plan(C.byref(h), arr, len(self.grids), C.byref(opts), self.device)
+        tun = None
+        if tuning is not None:
+            if len(tuning) != len(self.grids):
+                raise ValueError("one tuning dict per grid")
+            tun = (N.ibf_tuning * len(self.grids))()
+            for i, t in enumerate(tuning):
+                unknown = set(t or {}) - set(N.TUNING_FIELDS)
+                if unknown:
+                    raise ValueError(f"unknown tuning fields {sorted(unknown)}")
+                tun[i] = N.ibf_tuning(*(int((t or {}).get(f, 0)) for f in N.TUNING_FIELDS))
+        st = N.lib().ibf_projection_plan_tuned(C.byref(h), arr, len(self.grids), C.byref(opts), self.device, tun)
         N.check(st, "ibf_projection_plan")
         self._h = h
 
@@ -171,6 +183,12 @@ class Plan:
         if stats:
             return outs, {"max_div": st[0], "max_div_in": st[1], "compat": st[2]}
         return outs
+
+    def tuning(self, g=0):
+        """Launch shape grid g uses (dict of the ibf_tuning fields)."""
+        t = N.ibf_tuning()
+        N.check(N.lib().ibf_plan_get_tuning(self._h, int(g), C.byref(t)), "ibf_plan_get_tuning")
+        return {f: getattr(t, f) for f in N.TUNING_FIELDS}
 
     def sync_status(self):
         return N.lib().ibf_plan_sync_status(self._h)

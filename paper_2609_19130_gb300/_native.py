@@ -28,7 +28,8 @@ IBF_MAX_GRIDS = 4096
 # every entry point declared in include/ibf.h
 EXPORTS = ("ibf_projection_plan", "ibf_project", "ibf_project_backward", "ibf_plan_sync_status",
            "ibf_plan_destroy", "ibf_status_string", "ibf_last_error", "ibf_plan_get_info",
-           "ibf_profile_enable", "ibf_profile_read", "ibf_profile_reset", "ibf_project_noalloc")
+           "ibf_profile_enable", "ibf_profile_read", "ibf_profile_reset", "ibf_project_noalloc",
+           "ibf_projection_plan_tuned", "ibf_plan_get_tuning")
 
 
 class ibf_grid(C.Structure):
@@ -53,6 +54,14 @@ class ibf_stats(C.Structure):
 class ibf_plan_info(C.Structure):
     _fields_ = [("workspace_bytes", C.c_longlong), ("ngrids", C.c_int), ("precision", C.c_int),
                 ("refine_steps", C.c_int), ("total_cells", C.c_longlong)]
+
+
+class ibf_tuning(C.Structure):
+    _fields_ = [("rows", C.c_int), ("x_n1", C.c_int), ("y_n1", C.c_int), ("yz_kernel", C.c_int),
+                ("mb", C.c_int), ("tri", C.c_int)]
+
+
+TUNING_FIELDS = tuple(f for f, _ in ibf_tuning._fields_)
 
 
 class IBFError(RuntimeError):
@@ -102,6 +111,11 @@ def lib():
         L.ibf_project_noalloc.argtypes = [C.POINTER(ibf_grid), C.POINTER(ibf_opts), C.POINTER(ibf_fields),
                                           C.POINTER(ibf_fields), C.c_double, C.c_double, vp]
         L.ibf_project_noalloc.restype = C.c_int
+        L.ibf_projection_plan_tuned.argtypes = [C.POINTER(vp), C.POINTER(ibf_grid), C.c_int, C.POINTER(ibf_opts),
+                                                C.c_int, C.POINTER(ibf_tuning)]
+        L.ibf_projection_plan_tuned.restype = C.c_int
+        L.ibf_plan_get_tuning.argtypes = [vp, C.c_int, C.POINTER(ibf_tuning)]
+        L.ibf_plan_get_tuning.restype = C.c_int
         _lib = L
     return _lib
 

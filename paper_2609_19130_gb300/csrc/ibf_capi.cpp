@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -55,6 +57,7 @@ struct GridHost {
     ibf_grid g;
     std::vector<double> zf;
     GridDev d;
+    ibf_tuning tun;  // resolved launch shape
 };
 
 struct ProfRec {
@@ -72,8 +75,8 @@ struct ibf_plan {
     std::vector<GridHost> grids;
     std::vector<void *> allocs;
     Work work{};
-    size_t xsmem = 0, yzsmem = 0;
-    int nxblk = 0, nyzblk = 0, maxnz = 0;
+    size_t xsmem = 0, yzsmem = 0, slabsmem = 0;
+    int nxblk = 0, nyzblk = 0, nstrblk = 0, nslabblk = 0, maxnz = 0;
     long long ws_bytes = 0;
     long long total_cells = 0;
     cudaStream_t last_stream = nullptr;
@@ -196,7 +199,74 @@ ibf_status upload(const void *host, void *dev, size_t bytes) {
 
 #define IBF_TRY(x) do { ibf_status _s = (x); if (_s != IBF_OK) return _s; } while (0)
 
-ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
+// dynamic shared memory a kernel may request (the opt-in maximum less a margin for the
+// kernels' static shared memory)
+size_t smem_cap(const cudaDeviceProp &prop) { return (size_t)prop.sharedMemPerBlockOptin - 1024; }
+
+int ilog2_floor(int n) {
+    int l = 0;
+    while ((2 << l) <= n) ++l;
+    return l;
+}
+
+// Shared memory of the kernels for one grid under a launch shape.
+struct SmemNeed {
+    size_t x, yz, slab;
+};
+SmemNeed smem_need(const ibf_grid &g, int mixed, const ibf_tuning &t) {
+    const size_t csz = mixed ? 8 : 16, rsz = mixed ? 4 : 8;
+    const int nx2 = g.nx / t.x_n1, ny2 = g.ny / t.y_n1;
+    SmemNeed n{0, 0, 0};
+    n.x = (size_t)(t.rows / 2) * (size_t)(t.x_n1 * (nx2 + 1)) * csz;
+    const size_t sstr = (size_t)(t.y_n1 * (ny2 + 1) + 1), nslot = (size_t)g.ny * t.mb;
+    if (t.yz_kernel == 1) {
+        const size_t fwd = kYZStages * ((t.mb * sstr * csz + nslot * rsz + 15) & ~(size_t)15) + nslot * csz;
+        const size_t bwd = kYZStages * ((nslot * (csz + rsz) + 15) & ~(size_t)15) + (t.mb * sstr + nslot) * csz;
+        n.yz = std::max(fwd, bwd);
+    } else {
+        n.slab = (((size_t)g.nz * t.mb * sstr * csz) + 15) & ~(size_t)15;
+        if (t.tri > 1) n.slab += 3 * (size_t)g.nz * nslot * rsz;
+    }
+    return n;
+}
+
+bool fft_pair_ok(int n, int n1) { return n1 >= 1 && n % n1 == 0 && in_sizes(n1) && in_sizes(n / n1); }
+
+// Fill the fields of `t` left <= 0 with the default launch shape of grid g and check
+// the others.  The defaults: x kernels ~64 KB of FFT rows per CTA; balanced FFT
+// factors; streaming y/z kernels with enough x-modes per block for 64+ FFT tasks per
+// pass but at least one block per SM over the batch; Thomas with the pivot table.
+ibf_status resolve_tuning(const ibf_grid &g, int mixed, long long total_cols, int nsm, size_t cap,
+                          ibf_tuning *t) {
+    const int nxh = x_modes(g);
+    const int ny_even = (g.ny + 1) & ~1;
+    int a, b;
+    if (t->x_n1 <= 0) { factor(g.nx, &a, &b); t->x_n1 = a; }
+    if (t->y_n1 <= 0) { factor(g.ny, &a, &b); t->y_n1 = a; }
+    if (!fft_pair_ok(g.nx, t->x_n1) || !fft_pair_ok(g.ny, t->y_n1)) return IBF_ERR_UNSUPPORTED_SIZE;
+    if (t->rows <= 0) {
+        const int target = mixed ? 8192 : 4096;
+        t->rows = std::max(2, std::min(2 * std::max(1, target / g.nx), ny_even));
+    }
+    if (t->rows & 1) return IBF_ERR_UNSUPPORTED_SIZE;
+    t->rows = std::min(t->rows, std::max(2, ny_even));
+    if (t->yz_kernel <= 0) t->yz_kernel = 1;
+    if (t->yz_kernel > 2) return IBF_ERR_INVALID_ARG;
+    if (t->mb <= 0) {
+        const int ny2 = g.ny / t->y_n1;
+        const int mbmax = std::max(1, std::min(nxh, 4096 / g.ny));
+        const int want = (64 + ny2 - 1) / ny2;
+        t->mb = (int)std::min<long long>(std::min(mbmax, want), std::max<long long>(1, total_cols / nsm));
+    }
+    t->mb = std::min(t->mb, nxh);
+    if (t->tri <= 0) t->tri = 1;
+    if (t->tri > 1 + ilog2_floor(g.nz)) return IBF_ERR_INVALID_ARG;
+    const SmemNeed n = smem_need(g, mixed, *t);
+    if (n.x > cap || n.yz > cap || n.slab > cap) return IBF_ERR_UNSUPPORTED_SIZE;
+    return IBF_OK;
+}
+
+ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf_tuning *tuning) {
     const int mixed = pl->mixed;
     const size_t csz = mixed ? 8 : 16;   // complex element bytes
     const size_t rsz = mixed ? 4 : 8;    // real element bytes
@@ -210,9 +280,10 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
     for (int g = 0; g < ngrids; ++g) total_cols += x_modes(grids[g]);
 
     long long spec = 0, cells = 0;
-    int zoff = 0, poff = 0, xblk = 0, yzblk = 0;
+    int zoff = 0, poff = 0, xblk = 0, yzblk = 0, strblk = 0, slabblk = 0;
+    std::vector<int> str_start(ngrids + 1, 0), slab_start(ngrids + 1, 0);
     std::vector<double> twx_all, twy_all, tmp;
-    size_t maxx = 0, maxyz = 0;
+    size_t maxx = 0, maxyz = 0, maxslab = 0;
     for (int g = 0; g < ngrids; ++g) {
         GridHost &H = pl->grids[g];
         H.g = grids[g];
@@ -226,23 +297,16 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
         d.wall_y = H.g.bc_y == IBF_BC_NEUMANN;
         d.nxu = d.nx + d.wall_x;
         d.nyv = d.ny + d.wall_y;
-        factor(d.nx, &d.nx1, &d.nx2);
-        factor(d.ny, &d.ny1, &d.ny2);
-        // y-FFT + tridiagonal column blocks: at most 4096 modes per CTA (shared-memory state),
-        // enough blocks overall to fill the GPU twice.
-        // enough modes per block to keep the FFT passes' 64+ tasks busy, but at least one
-        // block per SM over the whole batch
-        const int mbmax = std::max(1, std::min(d.nxh, 4096 / d.ny));
-        const int want = (64 + d.ny2 - 1) / d.ny2;
-        int mb = (int)std::min<long long>(std::min(mbmax, want), std::max<long long>(1, total_cols / nsm));
-        d.mb = mb;
-        d.ncb = (d.nxh + mb - 1) / mb;
-        // x kernels: rows/2 complex sequences of length nx per CTA, ~64 KB of shared memory
-        const int target = mixed ? 8192 : 4096;
-        int rows = 2 * std::max(1, target / d.nx);
-        const int ny_even = (d.ny + 1) & ~1;
-        rows = std::min(rows, ny_even);
-        d.rows = std::max(2, rows);
+        ibf_tuning &t = H.tun;
+        t = tuning ? tuning[g] : ibf_tuning{0, 0, 0, 0, 0, 0};
+        IBF_TRY(resolve_tuning(H.g, mixed, total_cols, nsm, smem_cap(prop), &t));
+        d.nx1 = t.x_n1; d.nx2 = d.nx / t.x_n1;
+        d.ny1 = t.y_n1; d.ny2 = d.ny / t.y_n1;
+        d.mb = t.mb;
+        d.ncb = (d.nxh + d.mb - 1) / d.mb;
+        d.rows = t.rows;
+        d.yzk = t.yz_kernel - 1;
+        d.cr_levels = t.tri - 1;
         d.nrb = (d.ny + d.rows - 1) / d.rows;
         d.spec_off = spec;
         spec += (long long)d.nz * d.ncb * d.ny * d.mb;
@@ -273,6 +337,10 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
         xblk += d.nz * d.nrb;
         d.yzblk_off = yzblk;
         yzblk += d.ncb;
+        str_start[g] = strblk;
+        slab_start[g] = slabblk;
+        if (d.yzk == 0) strblk += d.ncb;
+        else slabblk += d.ncb;
         d.dx = H.g.lx / d.nx; d.dy = H.g.ly / d.ny;
         d.rdx = 1.0 / d.dx; d.rdy = 1.0 / d.dy;
         d.inv_nxy = 1.0 / ((double)d.nx * d.ny);
@@ -285,23 +353,27 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
         d.fmb = make_fdiv(d.mb);
         d.frows = make_fdiv(d.rows);
         d.fnpair = make_fdiv(d.rows / 2);
-        maxx = std::max(maxx, (size_t)(d.rows / 2) * (size_t)(d.nx1 * (d.nx2 + 1)) * csz);
-        {   // yz kernels: kYZStages pipeline stages (see k_yzfwd / k_yzbwd)
-            const size_t sstr = (size_t)(d.ny1 * (d.ny2 + 1) + 1), nslot = (size_t)d.ny * d.mb;
-            const size_t fwd = kYZStages * ((d.mb * sstr * csz + nslot * rsz + 15) & ~(size_t)15) + nslot * csz;
-            const size_t bwd = kYZStages * ((nslot * (csz + rsz) + 15) & ~(size_t)15) + (d.mb * sstr + nslot) * csz;
-            maxyz = std::max(maxyz, std::max(fwd, bwd));
+        {
+            const SmemNeed n = smem_need(H.g, mixed, t);
+            maxx = std::max(maxx, n.x);
+            maxyz = std::max(maxyz, n.yz);
+            maxslab = std::max(maxslab, n.slab);
         }
         pl->maxnz = std::max(pl->maxnz, d.nz);
         pl->total_cells += (long long)d.nx * d.ny * d.nz;
     }
-    if (maxx > (size_t)prop.sharedMemPerBlockOptin || maxyz > (size_t)prop.sharedMemPerBlockOptin ||
-        (size_t)10 * (pl->maxnz + 1) * 8 > (size_t)prop.sharedMemPerBlockOptin)
+    const size_t cap = smem_cap(prop);
+    if (maxx > cap || maxyz > cap || maxslab > cap || (size_t)10 * (pl->maxnz + 1) * 8 > cap)
         return IBF_ERR_UNSUPPORTED_SIZE;
+    str_start[ngrids] = strblk;
+    slab_start[ngrids] = slabblk;
     pl->xsmem = maxx;
     pl->yzsmem = maxyz;
+    pl->slabsmem = maxslab;
     pl->nxblk = xblk;
     pl->nyzblk = yzblk;
+    pl->nstrblk = strblk;
+    pl->nslabblk = slabblk;
 
     // per-level arrays
     const int nzt = zoff;
@@ -348,11 +420,16 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
     GridDev *dgrids;
     IBF_TRY(dalloc(pl, &dgrids, sizeof(GridDev) * ngrids));
     w.grids = dgrids;
-    int *dx, *dyz;
+    int *dx, *dyz, *dstr, *dslab;
     IBF_TRY(dalloc(pl, &dx, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dyz, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(dalloc(pl, &dstr, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(dalloc(pl, &dslab, sizeof(int) * (ngrids + 1)));
     w.xblk_start = dx;
     w.yzblk_start = dyz;
+    w.ystr_start = dstr;
+    w.slab_start = dslab;
+    IBF_TRY(dalloc(pl, &w.sol00, sizeof(double) * (size_t)zoff));
     IBF_TRY(dalloc(pl, &w.z.hz, sizeof(double) * nzt));
     IBF_TRY(dalloc(pl, &w.z.rhz, sizeof(double) * nzt));
     IBF_TRY(dalloc(pl, &w.z.rgzf, sizeof(double) * nzt));
@@ -396,6 +473,8 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids) {
     IBF_TRY(upload(hd.data(), dgrids, sizeof(GridDev) * ngrids));
     IBF_TRY(upload(xs.data(), dx, sizeof(int) * (ngrids + 1)));
     IBF_TRY(upload(ys.data(), dyz, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(upload(str_start.data(), dstr, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(upload(slab_start.data(), dslab, sizeof(int) * (ngrids + 1)));
     IBF_TRY(upload(hz.data(), w.z.hz, sizeof(double) * nzt));
     IBF_TRY(upload(rhz.data(), w.z.rhz, sizeof(double) * nzt));
     IBF_TRY(upload(rgzf.data(), w.z.rgzf, sizeof(double) * nzt));
@@ -499,9 +578,13 @@ ibf_status for_chunks(Ctx &c, const char *name, const ibf_fields *in, const ibf_
 ibf_status solve_core(Ctx &c, int first) {
     ibf_plan *pl = c.pl;
     const Work &w = pl->work;
-    IBF_TRY(timed(c, "yz_forward", [&]() { return launch_yzfwd(pl->mixed, w, pl->nyzblk, pl->yzsmem, c.st); }));
+    if (pl->nstrblk > 0)
+        IBF_TRY(timed(c, "yz_forward", [&]() { return launch_yzfwd(pl->mixed, w, pl->nstrblk, pl->yzsmem, c.st); }));
     IBF_TRY(timed(c, "mode00", [&]() { return launch_k00(w, pl->mixed, first, pl->maxnz, c.st); }));
-    IBF_TRY(timed(c, "yz_backward", [&]() { return launch_yzbwd(pl->mixed, w, pl->nyzblk, pl->yzsmem, c.st); }));
+    if (pl->nstrblk > 0)
+        IBF_TRY(timed(c, "yz_backward", [&]() { return launch_yzbwd(pl->mixed, w, pl->nstrblk, pl->yzsmem, c.st); }));
+    if (pl->nslabblk > 0)
+        IBF_TRY(timed(c, "yz_slab", [&]() { return launch_yzslab(pl->mixed, w, pl->nslabblk, pl->slabsmem, c.st); }));
     return IBF_OK;
 }
 
@@ -562,6 +645,174 @@ bool fields_ok(const ibf_fields *f, int n, bool need_p) {
     return true;
 }
 
+// Plan construction with resolved launch shapes (tuning: ngrids entries).
+ibf_status make_plan(ibf_plan **plan, const ibf_grid *grids, int ngrids, const ibf_opts *opts, int device,
+                     const ibf_tuning *tuning) {
+    ibf_plan *pl = new (std::nothrow) ibf_plan();
+    if (!pl) return IBF_ERR_OOM;
+    pl->device = device;
+    pl->ngrids = ngrids;
+    pl->opts = *opts;
+    pl->mixed = opts->precision == IBF_MIXED;
+    ibf_status s = build_plan(pl, grids, ngrids, tuning);
+    if (s != IBF_OK) {
+        cudaDeviceSynchronize();
+        free_all(pl);
+        delete pl;
+        return s;
+    }
+    *plan = pl;
+    return IBF_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+// Candidate launch shapes of one grid are timed as whole projections (one-grid plan,
+// zero fields, one warm-up and three timed calls on a private stream), by coordinate
+// descent: x-FFT factors, x rows per CTA, y-FFT factors, then the y/z kernel (streaming
+// with each column-block width; resident slab with each width and tridiagonal
+// algorithm that fits shared memory).  Results are cached per (shape, boundary
+// conditions, precision, refinement, forced fields) for the life of the process.
+struct TuneKey {
+    int v[13];
+    bool operator<(const TuneKey &o) const { return std::lexicographical_compare(v, v + 13, o.v, o.v + 13); }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, ibf_tuning> g_tune_cache;
+
+struct TuneBench {
+    int device;
+    ibf_opts opts;
+    ibf_grid g;
+    ibf_fields in, out;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+// projection time of grid b.g under shape t (ms), or a negative value if the shape
+// is not feasible
+float time_shape(TuneBench &b, const ibf_tuning &t) {
+    ibf_plan *p = nullptr;
+    if (make_plan(&p, &b.g, 1, &b.opts, b.device, &t) != IBF_OK) {
+        g_last_error.clear();
+        return -1.f;
+    }
+    float best = -1.f;
+    if (run(p, &b.in, &b.out, 1e-3, 1.0, nullptr, b.st, 0) == IBF_OK && cudaStreamSynchronize(b.st) == cudaSuccess) {
+        cudaEventRecord(b.e0, b.st);
+        bool ok = true;
+        for (int r = 0; r < 3 && ok; ++r) ok = run(p, &b.in, &b.out, 1e-3, 1.0, nullptr, b.st, 0) == IBF_OK;
+        cudaEventRecord(b.e1, b.st);
+        float ms = 0.f;
+        if (ok && cudaEventSynchronize(b.e1) == cudaSuccess && cudaEventElapsedTime(&ms, b.e0, b.e1) == cudaSuccess)
+            best = ms / 3.f;
+    }
+    cudaStreamSynchronize(b.st);
+    (void)cudaGetLastError();
+    free_all(p);
+    delete p;
+    return best;
+}
+
+ibf_status tune_grid(const ibf_grid &g, const ibf_opts &opts, int device, ibf_tuning *t) {
+    TuneKey key;
+    const int kv[13] = {g.nx, g.ny, g.nz, g.bc_x, g.bc_y, opts.precision, opts.refine_steps,
+                        t->rows, t->x_n1, t->y_n1, t->yz_kernel, t->mb, t->tri};
+    std::copy(kv, kv + 13, key.v);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { *t = it->second; return IBF_OK; }
+    }
+    const ibf_tuning forced = *t;
+    TuneBench b;
+    b.device = device;
+    b.opts = opts;
+    b.opts.autotune = 0;
+    b.g = g;
+    const size_t nxu = g.nx + (g.bc_x == IBF_BC_NEUMANN), nyv = g.ny + (g.bc_y == IBF_BC_NEUMANN);
+    const size_t bu = 8 * (size_t)g.nz * g.ny * nxu, bv = 8 * (size_t)g.nz * nyv * g.nx,
+                 bw = 8 * (size_t)(g.nz + 1) * g.ny * g.nx, bp = 8 * (size_t)g.nz * g.ny * g.nx;
+    double *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 2 * (bu + bv + bw) + bp);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); g_last_error = "autotune: cudaMalloc"; return IBF_ERR_OOM; }
+    unsigned char *c = reinterpret_cast<unsigned char *>(buf);
+    b.in = {(double *)c, (double *)(c + bu), (double *)(c + bu + bv), nullptr};
+    c += bu + bv + bw;
+    b.out = {(double *)c, (double *)(c + bu), (double *)(c + bu + bv), (double *)(c + bu + bv + bw)};
+    e = cudaMemset(buf, 0, 2 * (bu + bv + bw) + bp);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&b.e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b.e1);
+    ibf_status status = IBF_OK;
+    if (e != cudaSuccess) status = cuda_fail(e, "autotune setup");
+
+    ibf_tuning best = forced;
+    float tbest = -1.f;
+    auto consider = [&](ibf_tuning cand) {
+        const float ms = time_shape(b, cand);
+        if (ms > 0.f && (tbest < 0.f || ms < tbest)) { tbest = ms; best = cand; }
+    };
+    if (status == IBF_OK) {
+        {   // starting point: the defaults of the fields left free
+            cudaDeviceProp prop;
+            cudaGetDeviceProperties(&prop, device);
+            ibf_tuning d = forced;
+            if (resolve_tuning(g, opts.precision == IBF_MIXED, x_modes(g), prop.multiProcessorCount,
+                               smem_cap(prop), &d) == IBF_OK)
+                consider(d);
+        }
+        if (tbest > 0.f) {
+            static const int kRows[] = {2, 4, 8, 16, 32, 64};
+            static const int kMb[] = {1, 2, 4, 8, 16, 32};
+            if (forced.x_n1 <= 0)
+                for (int n1 : kFftSizes)
+                    if (n1 != best.x_n1 && fft_pair_ok(g.nx, n1)) { ibf_tuning c2 = best; c2.x_n1 = n1; consider(c2); }
+            if (forced.rows <= 0)
+                for (int r : kRows)
+                    if (r != best.rows && r <= ((g.ny + 1) & ~1)) { ibf_tuning c2 = best; c2.rows = r; consider(c2); }
+            if (forced.y_n1 <= 0)
+                for (int n1 : kFftSizes)
+                    if (n1 != best.y_n1 && fft_pair_ok(g.ny, n1)) { ibf_tuning c2 = best; c2.y_n1 = n1; consider(c2); }
+            const ibf_tuning base = best;
+            const int nxh = x_modes(g);
+            for (int kern = 1; kern <= 2; ++kern) {
+                if (forced.yz_kernel > 0 && forced.yz_kernel != kern) continue;
+                for (int mb : kMb) {
+                    if (mb > nxh && mb != 1) continue;
+                    if (forced.mb > 0 && forced.mb != mb) continue;
+                    const int ntri = kern == 1 ? 1 : 2 + ilog2_floor(g.nz);
+                    for (int tri = 1; tri <= ntri; ++tri) {
+                        if (forced.tri > 0 && forced.tri != tri) continue;
+                        if (kern == 2 && tri > 3 && tri != ntri) continue;  // Thomas, 1-2 levels, full reduction
+                        ibf_tuning c2 = base;
+                        c2.yz_kernel = kern;
+                        c2.mb = mb;
+                        c2.tri = tri;
+                        if (c2.yz_kernel == base.yz_kernel && c2.mb == base.mb && c2.tri == base.tri) continue;
+                        consider(c2);
+                    }
+                }
+            }
+        } else {
+            status = IBF_ERR_UNSUPPORTED_SIZE;
+        }
+    }
+    if (b.e0) cudaEventDestroy(b.e0);
+    if (b.e1) cudaEventDestroy(b.e1);
+    if (b.st) cudaStreamDestroy(b.st);
+    cudaFree(buf);
+    if (status != IBF_OK) return status;
+    *t = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+    return IBF_OK;
+}
+
+ibf_status autotune(const ibf_grid *grids, int ngrids, const ibf_opts &opts, int device, ibf_tuning *tun) {
+    for (int g = 0; g < ngrids; ++g) IBF_TRY(tune_grid(grids[g], opts, device, &tun[g]));
+    return IBF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -584,6 +835,11 @@ const char *ibf_status_string(ibf_status s) {
 const char *ibf_last_error(void) { return g_last_error.c_str(); }
 
 ibf_status ibf_projection_plan(ibf_plan **plan, const ibf_grid *grids, int ngrids, const ibf_opts *opts, int device) {
+    return ibf_projection_plan_tuned(plan, grids, ngrids, opts, device, nullptr);
+}
+
+ibf_status ibf_projection_plan_tuned(ibf_plan **plan, const ibf_grid *grids, int ngrids, const ibf_opts *opts,
+                                     int device, const ibf_tuning *tuning) {
     if (!plan) return IBF_ERR_INVALID_ARG;
     *plan = nullptr;
     if (!grids || !opts || ngrids < 1 || ngrids > IBF_MAX_GRIDS || device < 0) return IBF_ERR_INVALID_ARG;
@@ -595,23 +851,22 @@ ibf_status ibf_projection_plan(ibf_plan **plan, const ibf_grid *grids, int ngrid
         std::vector<double> zf;
         ibf_status s = validate(&grids[g], zf);
         if (s != IBF_OK) return s;
+        if (tuning) {
+            const ibf_tuning &t = tuning[g];
+            if (t.yz_kernel > 2 || (t.rows > 0 && (t.rows & 1))) return IBF_ERR_INVALID_ARG;
+        }
     }
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-    ibf_plan *pl = new (std::nothrow) ibf_plan();
-    if (!pl) return IBF_ERR_OOM;
-    pl->device = device;
-    pl->ngrids = ngrids;
-    pl->opts = *opts;
-    pl->mixed = opts->precision == IBF_MIXED;
-    ibf_status s = build_plan(pl, grids, ngrids);
-    if (s != IBF_OK) {
-        cudaDeviceSynchronize();
-        free_all(pl);
-        delete pl;
-        return s;
-    }
-    *plan = pl;
+    std::vector<ibf_tuning> tun(ngrids, ibf_tuning{0, 0, 0, 0, 0, 0});
+    if (tuning) std::copy(tuning, tuning + ngrids, tun.begin());
+    if (opts->autotune) IBF_TRY(autotune(grids, ngrids, *opts, device, tun.data()));
+    return make_plan(plan, grids, ngrids, opts, device, tun.data());
+}
+
+ibf_status ibf_plan_get_tuning(const ibf_plan *plan, int g, ibf_tuning *out) {
+    if (!plan || !out || g < 0 || g >= plan->ngrids) return IBF_ERR_INVALID_ARG;
+    *out = plan->grids[g].tun;
     return IBF_OK;
 }
 

@@ -12,6 +12,7 @@ constexpr int kGridsPerLaunch = 32;
 constexpr int kXThreads = 256;   // x-direction (row) kernels and stencil kernels
 constexpr int kYZThreads = 128;  // y-FFT + z-tridiagonal column kernels
 constexpr int kYZStages = 2;     // planes in flight per column block in the yz kernels
+constexpr int kSlabThreads = 256;  // resident-slab y/z kernel
 
 // Division by a run-time invariant d (Granlund & Montgomery, PLDI 1994, round-up
 // variant): n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31.
@@ -25,6 +26,8 @@ struct GridDev {
     int wall_x, wall_y;        // 1: that direction is wall-bounded (Neumann phi, DCT-II transform)
     int nxu, nyv;              // faces of u per row (nx + wall_x), rows of v per plane (ny + wall_y)
     int dctx_off, dcty_off;    // offsets of the exp(-i pi m/(2N)) tables of the DCTs (in twx / twy)
+    int yzk;                   // y/z kernel: 0 streaming (k_yzfwd + k_yzbwd), 1 resident slab (k_yzslab)
+    int cr_levels;             // slab kernel: cyclic-reduction levels before Thomas (0: Thomas with the table)
     int nx1, nx2, ny1, ny2;    // two-level FFT factors: nx = nx1*nx2, ny = ny1*ny2
     int mb, ncb;               // x-modes per column block of the yz kernels, number of blocks
     int rows, nrb;             // rows per CTA of the x kernels (even), row blocks per plane
@@ -58,7 +61,10 @@ struct Work {
     int ngrids;
     int walls;                 // some grid has a wall-bounded x or y (selects the kernels that handle it)
     const int *xblk_start;     // prefix of x-kernel blocks over grids [ngrids+1]
-    const int *yzblk_start;    // prefix of yz-kernel blocks over grids [ngrids+1]
+    const int *yzblk_start;    // prefix of column blocks over all grids [ngrids+1] (pivot table)
+    const int *ystr_start;     // prefix of column blocks over grids with streaming y/z kernels
+    const int *slab_start;     // prefix of column blocks over grids with the resident-slab kernel
+    double *sol00;             // per level (z_off + k): solution of the (0,0) mode, written by k_00
     ZArrays z;
     void *spec;                // complex<T> spectrum, per grid nz*ncb*ny*mb
     void *tab;                 // T pivot table, same layout as spec (real entries)
@@ -91,6 +97,7 @@ cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, i
 cudaError_t launch_yzfwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_yzbwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cudaStream_t st);
+cudaError_t launch_yzslab(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
                         size_t smem, cudaStream_t st);
 cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,

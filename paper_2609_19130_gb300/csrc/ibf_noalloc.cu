@@ -176,7 +176,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     // (one copy), then the workspace written by the kernels
     Carve cv;
     const size_t o_grid = cv.take(sizeof(GridDev));
-    const size_t o_xs = cv.take(2 * sizeof(int)), o_ys = cv.take(2 * sizeof(int));
+    const size_t o_xs = cv.take(2 * sizeof(int)), o_ys = cv.take(2 * sizeof(int)), o_slab = cv.take(2 * sizeof(int));
     const size_t L = (size_t)nz + 1;
     const size_t o_hz = cv.take(L * 8), o_rhz = cv.take(L * 8), o_rgzf = cv.take(L * 8), o_az = cv.take(L * 8),
                  o_cz = cv.take(L * 8), o_inv00 = cv.take(L * 8), o_azf = cv.take(L * 4), o_czf = cv.take(L * 4),
@@ -189,6 +189,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     const size_t npart = (size_t)nz * d.nrb;
     const size_t o_part = cv.take(8 * npart), o_partp = cv.take(8 * npart);
     const size_t o_mean = cv.take(8), o_maxb = cv.take(8), o_maxd = cv.take(8), o_err = cv.take(4);
+    const size_t o_sol00 = cv.take(8 * L);
     if (cv.off > kScratchBytes) return IBF_ERR_UNSUPPORTED_SIZE;
 
     unsigned char *base = nullptr;
@@ -204,6 +205,8 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     const int xs[2] = {0, nz * d.nrb}, ys[2] = {0, d.ncb};
     put(o_xs, xs, sizeof(xs));
     put(o_ys, ys, sizeof(ys));
+    const int none[2] = {0, 0};  // streaming y/z kernels only: no resident-slab blocks
+    put(o_slab, none, sizeof(none));
     std::vector<double> hz(L, 0.0), rhz(L, 0.0), rgzf(L, 0.0), az(L, 0.0), cz(L, 0.0), inv00(L, 0.0);
     std::vector<float> azf(L), czf(L), rhzdf(2 * L), rgzfdf(2 * L);
     for (int k = 0; k < nz; ++k) { hz[k] = zf[k + 1] - zf[k]; rhz[k] = 1.0 / hz[k]; }
@@ -247,6 +250,9 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     w.ngrids = 1;
     w.xblk_start = reinterpret_cast<const int *>(base + o_xs);
     w.yzblk_start = reinterpret_cast<const int *>(base + o_ys);
+    w.ystr_start = w.yzblk_start;
+    w.slab_start = reinterpret_cast<const int *>(base + o_slab);
+    w.sol00 = reinterpret_cast<double *>(base + o_sol00);
     w.z.hz = reinterpret_cast<double *>(base + o_hz);
     w.z.rhz = reinterpret_cast<double *>(base + o_rhz);
     w.z.rgzf = reinterpret_cast<double *>(base + o_rgzf);

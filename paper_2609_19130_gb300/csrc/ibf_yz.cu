@@ -76,9 +76,9 @@ __device__ __forceinline__ void dct_pre(cx<T> *buf, int nseq, int sstride, int N
 template <typename T, bool W>
 __global__ void __launch_bounds__(kYZThreads) k_yzfwd(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = find_grid(w.yzblk_start, w.ngrids, blockIdx.x);
+    const int g = find_grid(w.ystr_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
-    const int cb = blockIdx.x - __ldg(w.yzblk_start + g);
+    const int cb = blockIdx.x - __ldg(w.ystr_start + g);
     const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
     const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
@@ -150,9 +150,9 @@ __global__ void __launch_bounds__(kYZThreads) k_yzfwd(Work w) {
 template <typename T, bool W>
 __global__ void __launch_bounds__(kYZThreads) k_yzbwd(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = find_grid(w.yzblk_start, w.ngrids, blockIdx.x);
+    const int g = find_grid(w.ystr_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
-    const int cb = blockIdx.x - __ldg(w.yzblk_start + g);
+    const int cb = blockIdx.x - __ldg(w.ystr_start + g);
     const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
     const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
@@ -220,6 +220,205 @@ __global__ void __launch_bounds__(kYZThreads) k_yzbwd(Work w) {
         __syncthreads();
     }
     cp_async_wait<0>();
+}
+
+// ================================================================ k_yzslab
+// Whole z extent of one column block resident in shared memory: load every plane,
+// y-FFT of every plane, one tridiagonal solve per mode, inverse y-FFT, store.  The
+// spectrum is read and written once (the streaming kernels read and write it twice).
+// Shared memory: nz*mb padded FFT sequences, plane-major ([k][mm]); with cyclic
+// reduction also three real arrays a, b, c of nz*nslot entries ([k][slot]).
+//
+// Tridiagonal algorithms (cr = G.cr_levels):
+//   cr = 0: Thomas per mode with the plan's pivot table (as the streaming kernels);
+//   cr = S: S levels of cyclic reduction (Hockney 1965; in place: at stride s the
+//           equations i with (i+1) % 2s == 0 eliminate their neighbours i - s, i + s,
+//           which are not written at that level), Thomas on the nz >> S remaining
+//           equations of every mode, then S levels of back substitution.
+// The (0,0) mode takes the fp64 solution of k_00.
+template <typename T>
+__device__ __forceinline__ T slab_lambda(const GridDev &G, int m, int n);
+template <>
+__device__ __forceinline__ float slab_lambda<float>(const GridDev &G, int m, int n) {
+    const float sx = sinpif((float)m / (float)(G.wall_x ? 2 * G.nx : G.nx));
+    const float sy = sinpif((float)n / (float)(G.wall_y ? 2 * G.ny : G.ny));
+    return -4.f * (float)(G.rdx * G.rdx) * sx * sx - 4.f * (float)(G.rdy * G.rdy) * sy * sy;
+}
+template <>
+__device__ __forceinline__ double slab_lambda<double>(const GridDev &G, int m, int n) {
+    const double sx = sinpi((double)m / (G.wall_x ? 2 * G.nx : G.nx));
+    const double sy = sinpi((double)n / (G.wall_y ? 2 * G.ny : G.ny));
+    return -4.0 * G.rdx * G.rdx * sx * sx - 4.0 * G.rdy * G.rdy * sy * sy;
+}
+
+template <typename T, bool W>
+__global__ void __launch_bounds__(kSlabThreads) k_yzslab(Work w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = find_grid(w.slab_start, w.ngrids, blockIdx.x);
+    const GridDev &G = w.grids[g];
+    const int cb = blockIdx.x - __ldg(w.slab_start + g);
+    const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
+    const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
+    const int nslot = ny * mb;
+    const int nvalid = min(mb, nxh - cb * mb);
+    const int wall_y = W ? G.wall_y : 0;
+    const cx<T> *twy = reinterpret_cast<const cx<T> *>(w.twy) + G.twy_off;
+    const cx<T> *dcty = reinterpret_cast<const cx<T> *>(w.twy) + G.dcty_off;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nseq = nz * mb;
+    const size_t kst = (size_t)mb * sstride;  // distance between planes of one slot
+    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
+    const int total = nz * nslot;
+
+    for (int t = tid; t < total; t += nthr) {
+        const int k = t / nslot, q = t - k * nslot;
+        const int j = (int)fdiv((unsigned)q, fmb), mm = q - j * mb;
+        cx<T> v = {(T)0, (T)0};
+        if (mm < nvalid) v = spec[((size_t)k * ncb + cb) * nslot + q];
+        buf[k * kst + mm * sstride + pos_nat(wall_y ? dct_perm(j, ny) : j, fN2)] = v;
+    }
+    __syncthreads();
+    fft_batch<T, -1>(buf, nseq, sstride, N1, N2, fN1, fN2, twy);
+    if (wall_y) dct_post<T>(buf, nseq, sstride, ny, N1, N2, fN1, dcty);
+
+    const T *az = zarr<T>(w.z.az, w.z.azf) + G.z_off;
+    const T *cz = zarr<T>(w.z.cz, w.z.czf) + G.z_off;
+    const double *s00 = w.sol00 + G.z_off;
+    const int S = G.cr_levels;
+    if (S == 0) {
+        const T *tab = reinterpret_cast<const T *>(w.tab) + G.tab_off;
+        for (int q = tid; q < nslot; q += nthr) {
+            const int sn = (int)fdiv((unsigned)q, fmb), mm = q - sn * mb;
+            cx<T> *col = buf + mm * sstride + pos_nat(sn, fN2);
+            if (mm >= nvalid) continue;
+            if (cb == 0 && q == 0) {
+                for (int k = 0; k < nz; ++k) col[k * kst] = {(T)s00[k], (T)0};
+                continue;
+            }
+            const T *tq = tab + (size_t)cb * nslot + q;
+            const size_t tst = (size_t)ncb * nslot;
+            cx<T> dp = {(T)0, (T)0};
+#pragma unroll 4
+            for (int k = 0; k < nz; ++k) {
+                const T inv = tq[k * tst], a = az[k];
+                const cx<T> r = col[k * kst];
+                dp = {(r.x - a * dp.x) * inv, (r.y - a * dp.y) * inv};
+                col[k * kst] = dp;
+            }
+            cx<T> ph = {(T)0, (T)0};
+#pragma unroll 4
+            for (int k = nz - 1; k >= 0; --k) {
+                const T cp = cz[k] * tq[k * tst];
+                const cx<T> d = col[k * kst];
+                ph = {d.x - cp * ph.x, d.y - cp * ph.y};
+                col[k * kst] = ph;
+            }
+        }
+    } else {
+        T *Ar = reinterpret_cast<T *>(smem_raw + (((size_t)nseq * sstride * sizeof(cx<T>) + 15) & ~(size_t)15));
+        T *Br = Ar + total, *Cr = Br + total;
+        // coefficients of every (level, slot); the singular and padding slots become identity rows
+        for (int t = tid; t < total; t += nthr) {
+            const int k = t / nslot, q = t - k * nslot;
+            const int sn = (int)fdiv((unsigned)q, fmb), mm = q - sn * mb;
+            const int m = cb * mb + mm, n = (sn / N2) + N1 * (sn - (sn / N2) * N2);
+            cx<T> *e = buf + k * kst + mm * sstride + pos_nat(sn, fN2);
+            if (mm >= nvalid || (cb == 0 && q == 0)) {
+                Ar[t] = (T)0; Br[t] = (T)1; Cr[t] = (T)0;
+                *e = {(mm < nvalid) ? (T)s00[k] : (T)0, (T)0};
+            } else {
+                const T a = az[k], c = cz[k];
+                Ar[t] = a; Cr[t] = c; Br[t] = -(a + c) + slab_lambda<T>(G, m, n);
+            }
+        }
+        __syncthreads();
+        auto D = [&](int k, int q) -> cx<T> & {
+            const int sn = (int)fdiv((unsigned)q, fmb), mm = q - sn * mb;
+            return buf[k * kst + mm * sstride + pos_nat(sn, fN2)];
+        };
+        for (int l = 0; l < S; ++l) {  // reduction: kept equations i = 2s(r+1) - 1
+            const int s = 1 << l, s2 = s << 1, nk = nz / s2;
+            for (int t = tid; t < nk * nslot; t += nthr) {
+                const int r = t / nslot, q = t - r * nslot;
+                const int i = s2 * (r + 1) - 1, im = i - s, ip = i + s;
+                const int ti = i * nslot + q, tm = im * nslot + q, tp = ip * nslot + q;
+                const T al = -Ar[ti] / Br[tm];
+                cx<T> &di = D(i, q);
+                const cx<T> dm = D(im, q);
+                T na = al * Ar[tm], nb = Br[ti] + al * Cr[tm], nc = (T)0;
+                cx<T> nd = {di.x + al * dm.x, di.y + al * dm.y};
+                if (ip < nz) {
+                    const T ga = -Cr[ti] / Br[tp];
+                    const cx<T> dq = D(ip, q);
+                    nc = ga * Cr[tp];
+                    nb += ga * Ar[tp];
+                    nd = {nd.x + ga * dq.x, nd.y + ga * dq.y};
+                }
+                Ar[ti] = na; Br[ti] = nb; Cr[ti] = nc;
+                di = nd;
+            }
+            __syncthreads();
+        }
+        {   // Thomas on the reduced systems: equations 2^S (r+1) - 1, r < nz >> S
+            const int st = 1 << S, R = nz >> S;
+            for (int q = tid; q < nslot; q += nthr) {
+                T cprev = (T)0;
+                cx<T> dprev = {(T)0, (T)0};
+                for (int r = 0; r < R; ++r) {
+                    const int i = st * (r + 1) - 1, ti = i * nslot + q;
+                    const T a = Ar[ti];
+                    const T inv = (T)1 / (Br[ti] - a * cprev);
+                    cx<T> &d = D(i, q);
+                    dprev = {(d.x - a * dprev.x) * inv, (d.y - a * dprev.y) * inv};
+                    cprev = Cr[ti] * inv;
+                    Cr[ti] = cprev;
+                    d = dprev;
+                }
+                cx<T> x = {(T)0, (T)0};
+                for (int r = R - 1; r >= 0; --r) {
+                    const int i = st * (r + 1) - 1;
+                    cx<T> &d = D(i, q);
+                    const T c = Cr[i * nslot + q];
+                    x = {d.x - c * x.x, d.y - c * x.y};
+                    d = x;
+                }
+            }
+            __syncthreads();
+        }
+        for (int l = S - 1; l >= 0; --l) {  // back substitution of the equations eliminated at level l
+            const int s = 1 << l, cnt = (nz / s + 1) >> 1;
+            for (int t = tid; t < cnt * nslot; t += nthr) {
+                const int r = t / nslot, q = t - r * nslot;
+                const int i = s * (2 * r + 1) - 1;
+                if (i >= nz) continue;
+                const int ti = i * nslot + q;
+                cx<T> &d = D(i, q);
+                cx<T> v = d;
+                if (i - s >= 0) {
+                    const cx<T> xm = D(i - s, q);
+                    v = {v.x - Ar[ti] * xm.x, v.y - Ar[ti] * xm.y};
+                }
+                if (i + s < nz) {
+                    const cx<T> xp = D(i + s, q);
+                    v = {v.x - Cr[ti] * xp.x, v.y - Cr[ti] * xp.y};
+                }
+                const T inv = (T)1 / Br[ti];
+                d = {v.x * inv, v.y * inv};
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (wall_y) dct_pre<T>(buf, nseq, sstride, ny, N1, N2, fN1, dcty);
+    fft_batch<T, +1>(buf, nseq, sstride, N1, N2, fN1, fN2, twy);
+    for (int t = tid; t < total; t += nthr) {
+        const int k = t / nslot, q = t - k * nslot;
+        const int j = (int)fdiv((unsigned)q, fmb), mm = q - j * mb;
+        if (mm < nvalid)
+            spec[((size_t)k * ncb + cb) * nslot + q] = buf[k * kst + mm * sstride + pos_nat(wall_y ? dct_perm(j, ny) : j, fN2)];
+    }
 }
 
 // ================================================================ k_00 (fp64, one CTA per grid)
@@ -319,7 +518,13 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     const double mphi = rhs[nz];
     cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
     const size_t stride = (size_t)G.ncb * G.ny * G.mb;
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) spec[(size_t)k * stride] = {(T)(rhs[k] - mphi), (T)0};
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        const double v = rhs[k] - mphi;
+        // streaming kernels: slot (0,0) of the y-transformed spectrum; the slab kernel
+        // (whose spectrum is still untransformed in y here) reads sol00
+        if (G.yzk == 0) spec[(size_t)k * stride] = {(T)v, (T)0};
+        w.sol00[zo + k] = v;
+    }
 }
 
 // Pivots of every mode's tridiagonal system (fp64 arithmetic, stored as T):
@@ -387,6 +592,18 @@ cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cud
     return cudaGetLastError();
 }
 
+cudaError_t launch_yzslab(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    if (mixed) {
+        if (w.walls) k_yzslab<float, true><<<grid1(nblk), kSlabThreads, smem, st>>>(w);
+        else k_yzslab<float, false><<<grid1(nblk), kSlabThreads, smem, st>>>(w);
+    } else {
+        if (w.walls) k_yzslab<double, true><<<grid1(nblk), kSlabThreads, smem, st>>>(w);
+        else k_yzslab<double, false><<<grid1(nblk), kSlabThreads, smem, st>>>(w);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t st) {
     if (mixed) k_build_table<float><<<grid1(nblk), 256, 0, st>>>(w);
     else k_build_table<double><<<grid1(nblk), 256, 0, st>>>(w);
@@ -403,9 +620,11 @@ cudaError_t set_smem_limits_yz(int mixed) {
         if (mixed) {
             set((const void *)k_yzfwd<float, W>);
             set((const void *)k_yzbwd<float, W>);
+            set((const void *)k_yzslab<float, W>);
         } else {
             set((const void *)k_yzfwd<double, W>);
             set((const void *)k_yzbwd<double, W>);
+            set((const void *)k_yzslab<double, W>);
         }
     };
     set_all(std::false_type{});

@@ -109,3 +109,16 @@ def test_valid_plan_without_gpu_reports_cuda_error(lib):
     assert st == N.IBF_ERR_CUDA
     assert not h.value
     assert N.last_error()
+
+
+@pytest.mark.parametrize("bad", [dict(rows=3), dict(yz_kernel=3)])
+def test_tuning_validation_on_host(lib, bad):
+    """Forced launch shapes are checked on the host before the device is touched."""
+    g = (N.ibf_grid * 1)()
+    g[0] = N.ibf_grid(16, 16, 8, 1.0, 1.0, 1.0, None, 0.0, 0, 0, 1, 1)
+    t = (N.ibf_tuning * 1)()
+    t[0] = N.ibf_tuning(*(bad.get(f, 0) for f in N.TUNING_FIELDS))
+    h = C.c_void_p()
+    o = N.ibf_opts(1, 1, 0, 0)
+    assert N.lib().ibf_projection_plan_tuned(C.byref(h), g, 1, C.byref(o), 0, t) == N.IBF_ERR_INVALID_ARG
+    assert not h.value

@@ -30,8 +30,12 @@ def config3_grids():
 
 
 def test_config3_graph_replay_matches_eager_and_oracle():
+    """64 uneven grids, mixed precision with refinement, launch shapes autotuned per
+    grid shape (tridiagonal variant, column blocks, FFT factors, row blocks)."""
     grids = config3_grids()
-    plan = Plan(grids, precision=MIXED, refine_steps=1)
+    plan = Plan(grids, precision=MIXED, refine_steps=1, autotune=True)
+    tunings = [plan.tuning(g) for g in range(len(grids))]
+    assert all(all(v > 0 for v in t.values()) for t in tunings)
     ins, outs, outs_g = [], [], []
     for i, g in enumerate(grids):
         u, v, w = synth.uniform_velocity_torch(1000 + i, g.nx, g.ny, g.nz, "cuda")
@@ -74,6 +78,14 @@ def test_config3_graph_replay_matches_eager_and_oracle():
         phi, *_ = O.project(og, *(t.cpu().numpy() for t in ins[i]), dt=1e-3)
         assert rel_l2(outs[i][3].cpu().numpy(), phi) <= 1e-9
     plan.close()
+    # the default launch shapes give the same projection (to the mixed tolerance)
+    plan_d = Plan(grids, precision=MIXED, refine_steps=1)
+    outs_d = [tuple(torch.empty_like(t) for t in o) for o in outs]
+    plan_d.project_into(ins, outs_d, 1e-3, 1.0)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, outs_d):
+        assert float(torch.linalg.norm(a[3] - b[3]) / torch.linalg.norm(b[3])) <= 2e-9
+    plan_d.close()
 
 
 def test_config5_finite_differences_batch8_256cube():
