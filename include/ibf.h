@@ -73,6 +73,18 @@ typedef enum ibf_bc {
     IBF_BC_DIRICHLET = 2          /* homogeneous Dirichlet phi (not implemented: UNSUPPORTED_BC) */
 } ibf_bc;
 
+/* Output pressure (paper Eq. pressure).  IBF_P_PHI: out.p = phi.  IBF_P_EXPLICIT:
+ * out.p = p_n + phi (explicit viscous terms).  IBF_P_IMPLICIT: out.p = p_n + phi -
+ * alpha dt / (2 Re) lap(phi) (Crank-Nicolson viscous terms), with lap(phi) taken as
+ * the right-hand side the solve satisfies, b - <b> (b = D u* / (alpha dt)), which is
+ * the discrete Laplacian of the returned phi up to the solver's residual.  p_n is
+ * in[g].p (required for the last two); out.p may alias it. */
+typedef enum ibf_pressure {
+    IBF_P_PHI = 0,
+    IBF_P_EXPLICIT = 1,
+    IBF_P_IMPLICIT = 2
+} ibf_pressure;
+
 typedef enum ibf_precision {
     IBF_FP64 = 0,  /* fp64 transforms, tridiagonal sweeps and stencils */
     IBF_MIXED = 1  /* fp32 transforms and sweeps; float-float (2 x fp32) stencils, residual and
@@ -96,8 +108,11 @@ typedef struct ibf_opts {
     int refine_steps;       /* IBF_MIXED only: iterative-refinement sweeps after the first solve (0..8) */
     int autotune;           /* 1: time candidate launch shapes (ibf_tuning) at plan time, once per
                                distinct grid shape and precision in the process (allocates
-                               temporary device buffers, synchronises the device) */
-    int reserved;           /* must be 0 */
+                               temporary device buffers, synchronises the device); with the
+                               environment variable IBF_AUTOTUNE_LOG set, every timed
+                               candidate is printed to stderr */
+    int pressure;           /* what out.p receives (Eq. pressure), ibf_pressure; default IBF_P_PHI */
+    double inv_re;          /* 1/Re of the implicit viscous term (IBF_P_IMPLICIT; >= 0) */
 } ibf_opts;
 
 /* DEVICE pointers (float64, layouts above) of one grid. */
@@ -126,7 +141,8 @@ ibf_status ibf_projection_plan(ibf_plan **plan, const ibf_grid *grids, int ngrid
                                const ibf_opts *opts, int device);
 
 /* Project grid g's u* = in[g] into out[g] (arrays of ngrids ibf_fields):
- * out.p <- phi, out.u/v/w <- u* - alpha dt G phi.  in[g].p is ignored.  out may
+ * out.p <- phi (or the pressure update chosen by opts->pressure, reading p_n from
+ * in[g].p; otherwise in[g].p is ignored), out.u/v/w <- u* - alpha dt G phi.  out may
  * alias in (in place).  dt > 0, alpha > 0.  stats may be NULL.  stream is a
  * cudaStream_t (NULL: legacy default stream).  Enqueues kernels only: no
  * allocation, no host synchronisation, so it can be captured into a CUDA graph.
@@ -139,7 +155,8 @@ ibf_status ibf_project(ibf_plan *plan, const ibf_fields *in, const ibf_fields *o
  * Euclidean inner product:  grad_in = g_u + D^T S^-T (g_phi/(alpha dt) - G^T g_u),
  * S^-T = V S^-1 V^-1 with V = diag(dx dy hz_k), computed with the same solver.
  * grad_out[g].{u,v,w} = g_u (device, same shapes as the velocity), grad_out[g].p = g_phi
- * (may be NULL = zero).  grad_in[g].{u,v,w} receive the gradient with respect to u*
+ * (may be NULL = zero).  The adjoint is that of the phi output: opts->pressure does not
+ * enter it.  grad_in[g].{u,v,w} receive the gradient with respect to u*
  * (grad_in[g].p ignored).  grad_in may alias grad_out's velocity arrays.  Same
  * stream/capture rules as ibf_project. */
 ibf_status ibf_project_backward(ibf_plan *plan, const ibf_fields *grad_out, const ibf_fields *grad_in,
@@ -154,7 +171,9 @@ ibf_status ibf_project_backward(ibf_plan *plan, const ibf_fields *grad_out, cons
  *   yz_kernel : 1 streaming y/z kernels (y-FFT fused with Thomas sweeps that stream
  *               the planes, the spectrum read and written twice), 2 resident slab
  *               (the whole z extent of a column block in shared memory: one read,
- *               one write; small grids only);
+ *               one write; small grids only), 3 split (y-FFT of every (plane, column
+ *               block) in its own CTA, then Thomas sweeps with one thread per mode:
+ *               the spectrum read and written four times, all of it streamed);
  *   mb        : x-modes per column block of the y/z kernels;
  *   tri       : tridiagonal algorithm of the slab kernel: 1 Thomas per mode with the
  *               plan's pivot table, 1 + S (S >= 1) S levels of in-place cyclic
@@ -224,6 +243,7 @@ ibf_status ibf_profile_reset(ibf_plan *plan);
  * calls that overlap on the GPU (other streams, other host threads) race and corrupt
  * each other: order them.  The first call on a device looks up the array's device
  * address and caches it; make that first call before any stream capture.
+ * opts->pressure must be IBF_P_PHI.
  * Errors: INVALID_ARG, UNSUPPORTED_BC, UNSUPPORTED_SIZE (also when the workspace
  * of the grid does not fit in IBF_NOALLOC_SCRATCH_BYTES: about 2.5 million cells in
  * IBF_MIXED, 4.5 million in IBF_FP64), CUDA. */

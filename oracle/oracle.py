@@ -146,6 +146,13 @@ def project(g: Grid, us, vs, ws, dt=1e-3, alpha=1.0):
     return phi, u, v, w, st
 
 
+def pressure_update(g: Grid, p_n, phi, dt=1e-3, alpha=1.0, inv_re=0.0):
+    """Eq. (pressure) (Section "Fluid Mechanics"): p_{n+1} = p_n + phi - alpha dt/(2 Re) lap(phi),
+    with the discrete Laplacian L = D G of the projection; inv_re = 0 is the explicit-viscous
+    update p_n + phi."""
+    return p_n + phi - 0.5 * alpha * dt * inv_re * laplacian(g, phi)
+
+
 def project_adjoint(g: Grid, gu, gv, gw, gphi=None, dt=1e-3, alpha=1.0):
     su, sv, sw = g.shapes
     a, b, c = np.empty(su), np.empty(sv), np.empty(sw)

@@ -79,9 +79,11 @@ class Plan:
     """A projection plan for a batch of grids on one device (owns its workspace)."""
 
     def __init__(self, grids, precision: str = MIXED, refine_steps: int = 1, device: int | None = None,
-                 autotune: bool = False, tuning=None):
+                 autotune: bool = False, tuning=None, pressure: int = N.IBF_P_PHI, inv_re: float = 0.0):
         """tuning: None, or one dict per grid with any of the ibf_tuning fields (rows,
-        x_n1, y_n1, yz_kernel, mb, tri) to force; the rest default (or are autotuned)."""
+        x_n1, y_n1, yz_kernel, mb, tri) to force; the rest default (or are autotuned).
+        pressure: IBF_P_PHI (p output = phi), IBF_P_EXPLICIT (p_n + phi) or IBF_P_IMPLICIT
+        (p_n + phi - alpha dt/(2 Re) lap phi, inv_re = 1/Re); p_n is the 4th input field."""
         if isinstance(grids, Grid):
             grids = [grids]
         self.grids = list(grids)
@@ -100,7 +102,9 @@ class Plan:
                 self._zf_keep.append(z)
                 zf = z.ctypes.data_as(C.POINTER(C.c_double))
             arr[i] = N.ibf_grid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, zf, g.beta, g.bc_x, g.bc_y, g.bc_zlo, g.bc_zhi)
-        opts = N.ibf_opts(N.IBF_MIXED if precision == MIXED else N.IBF_FP64, self.refine_steps, int(autotune), 0)
+        self.pressure = int(pressure)
+        opts = N.ibf_opts(N.IBF_MIXED if precision == MIXED else N.IBF_FP64, self.refine_steps, int(autotune),
+                          self.pressure, float(inv_re))
         h = C.c_void_p()
         tun = None
         if tuning is not None:
@@ -128,8 +132,11 @@ class Plan:
         fout = (N.ibf_fields * n)()
         for g in range(n):
             u, v, w = ins[g][:3]
+            pn = ins[g][3] if len(ins[g]) > 3 else None
+            if self.pressure != N.IBF_P_PHI and pn is None:
+                raise ValueError("this plan updates the pressure: pass (u, v, w, p_n) per grid")
             uo, vo, wo, po = outs[g]
-            fin[g] = N.ibf_fields(u.data_ptr(), v.data_ptr(), w.data_ptr(), None)
+            fin[g] = N.ibf_fields(u.data_ptr(), v.data_ptr(), w.data_ptr(), pn.data_ptr() if pn is not None else None)
             fout[g] = N.ibf_fields(uo.data_ptr(), vo.data_ptr(), wo.data_ptr(), po.data_ptr())
         st_ptr = None
         if stats is not None:
@@ -151,13 +158,14 @@ class Plan:
         N.check(s, "ibf_project_backward")
 
     # ------------------------------------------------------------ conveniences
-    def project(self, u, v, w, dt, alpha=1.0, out=None, stats=False, stream=None):
-        """Single-grid convenience: returns (u, v, w, p) (new tensors unless `out` is given)."""
+    def project(self, u, v, w, dt, alpha=1.0, out=None, stats=False, stream=None, p=None):
+        """Single-grid convenience: returns (u, v, w, p) (new tensors unless `out` is given);
+        `p` is p_n for plans with a pressure update."""
         import torch
         if len(self.grids) != 1:
             raise ValueError("project() is for single-grid plans; use project_batch()")
-        res = self.project_batch([(u, v, w)], dt, alpha, out=[out] if out is not None else None,
-                                 stats=stats, stream=stream)
+        res = self.project_batch([(u, v, w) if p is None else (u, v, w, p)], dt, alpha,
+                                 out=[out] if out is not None else None, stats=stats, stream=stream)
         return res[0] if not stats else (res[0][0], res[1])
 
     def project_batch(self, fields, dt, alpha=1.0, out=None, stats=False, stream=None):
@@ -169,6 +177,8 @@ class Plan:
             su, sv, sw = grid.shapes
             for t, sh, nm in zip(f[:3], (su, sv, sw), ("u", "v", "w")):
                 _check_field(t, sh, nm)
+            if len(f) > 3 and f[3] is not None:
+                _check_field(f[3], (grid.nz, grid.ny, grid.nx), "p")
             if out is not None:
                 o = out[g]
             else:

@@ -23,6 +23,7 @@ IBF_ERR_UNSUPPORTED_BC = 8
 
 IBF_BC_PERIODIC, IBF_BC_NEUMANN, IBF_BC_DIRICHLET = 0, 1, 2
 IBF_FP64, IBF_MIXED = 0, 1
+IBF_P_PHI, IBF_P_EXPLICIT, IBF_P_IMPLICIT = 0, 1, 2
 IBF_MAX_GRIDS = 4096
 
 # every entry point declared in include/ibf.h
@@ -40,7 +41,8 @@ class ibf_grid(C.Structure):
 
 
 class ibf_opts(C.Structure):
-    _fields_ = [("precision", C.c_int), ("refine_steps", C.c_int), ("autotune", C.c_int), ("reserved", C.c_int)]
+    _fields_ = [("precision", C.c_int), ("refine_steps", C.c_int), ("autotune", C.c_int), ("pressure", C.c_int),
+                ("inv_re", C.c_double)]
 
 
 class ibf_fields(C.Structure):

@@ -75,8 +75,8 @@ struct ibf_plan {
     std::vector<GridHost> grids;
     std::vector<void *> allocs;
     Work work{};
-    size_t xsmem = 0, yzsmem = 0, slabsmem = 0;
-    int nxblk = 0, nyzblk = 0, nstrblk = 0, nslabblk = 0, maxnz = 0;
+    size_t xsmem = 0, yzsmem = 0, slabsmem = 0, yfftsmem = 0;
+    int nxblk = 0, nyzblk = 0, nstrblk = 0, nslabblk = 0, nyfftblk = 0, nsweepblk = 0, maxnz = 0;
     long long ws_bytes = 0;
     long long total_cells = 0;
     cudaStream_t last_stream = nullptr;
@@ -89,15 +89,23 @@ struct ibf_plan {
 
 namespace {
 
-template <typename P> ibf_status dalloc(ibf_plan *pl, P **out, size_t bytes) {
-    static int fault_countdown = -2;
-    if (fault_countdown == -2) {
-        const char *f = getenv("IBF_FAULT_OOM_AT");  // test hook: fail the N-th plan allocation
-        fault_countdown = f ? atoi(f) : -1;
+// Test hook: IBF_FAULT_OOM_AT=n makes the n-th plan allocation of the process fail
+// (one counter for every allocation, whatever its element type).
+bool inject_alloc_failure() {
+    static std::mutex mu;
+    static int countdown = -2;
+    std::lock_guard<std::mutex> lk(mu);
+    if (countdown == -2) {
+        const char *f = getenv("IBF_FAULT_OOM_AT");
+        countdown = f ? atoi(f) : -1;
     }
+    return countdown > 0 && --countdown == 0;
+}
+
+template <typename P> ibf_status dalloc(ibf_plan *pl, P **out, size_t bytes) {
     *out = nullptr;
     if (bytes == 0) bytes = 16;
-    if (fault_countdown > 0 && --fault_countdown == 0) {
+    if (inject_alloc_failure()) {
         g_last_error = "injected allocation failure";
         return IBF_ERR_OOM;
     }
@@ -211,21 +219,23 @@ int ilog2_floor(int n) {
 
 // Shared memory of the kernels for one grid under a launch shape.
 struct SmemNeed {
-    size_t x, yz, slab;
+    size_t x, yz, slab, yfft;
 };
 SmemNeed smem_need(const ibf_grid &g, int mixed, const ibf_tuning &t) {
     const size_t csz = mixed ? 8 : 16, rsz = mixed ? 4 : 8;
     const int nx2 = g.nx / t.x_n1, ny2 = g.ny / t.y_n1;
-    SmemNeed n{0, 0, 0};
+    SmemNeed n{0, 0, 0, 0};
     n.x = (size_t)(t.rows / 2) * (size_t)(t.x_n1 * (nx2 + 1)) * csz;
     const size_t sstr = (size_t)(t.y_n1 * (ny2 + 1) + 1), nslot = (size_t)g.ny * t.mb;
-    if (t.yz_kernel == 1) {
+    if (t.yz_kernel == 1) {  // layouts of k_yzfwd / k_yzbwd
         const size_t fwd = kYZStages * ((t.mb * sstr * csz + nslot * rsz + 15) & ~(size_t)15) + nslot * csz;
         const size_t bwd = kYZStages * ((nslot * (csz + rsz) + 15) & ~(size_t)15) + (t.mb * sstr + nslot) * csz;
         n.yz = std::max(fwd, bwd);
-    } else {
+    } else if (t.yz_kernel == 2) {
         n.slab = (((size_t)g.nz * t.mb * sstr * csz) + 15) & ~(size_t)15;
         if (t.tri > 1) n.slab += 3 * (size_t)g.nz * nslot * rsz;
+    } else {
+        n.yfft = (size_t)t.mb * sstr * csz;
     }
     return n;
 }
@@ -251,7 +261,7 @@ ibf_status resolve_tuning(const ibf_grid &g, int mixed, long long total_cols, in
     if (t->rows & 1) return IBF_ERR_UNSUPPORTED_SIZE;
     t->rows = std::min(t->rows, std::max(2, ny_even));
     if (t->yz_kernel <= 0) t->yz_kernel = 1;
-    if (t->yz_kernel > 2) return IBF_ERR_INVALID_ARG;
+    if (t->yz_kernel > 3) return IBF_ERR_INVALID_ARG;
     if (t->mb <= 0) {
         const int ny2 = g.ny / t->y_n1;
         const int mbmax = std::max(1, std::min(nxh, 4096 / g.ny));
@@ -262,7 +272,7 @@ ibf_status resolve_tuning(const ibf_grid &g, int mixed, long long total_cols, in
     if (t->tri <= 0) t->tri = 1;
     if (t->tri > 1 + ilog2_floor(g.nz)) return IBF_ERR_INVALID_ARG;
     const SmemNeed n = smem_need(g, mixed, *t);
-    if (n.x > cap || n.yz > cap || n.slab > cap) return IBF_ERR_UNSUPPORTED_SIZE;
+    if (n.x > cap || n.yz > cap || n.slab > cap || n.yfft > cap) return IBF_ERR_UNSUPPORTED_SIZE;
     return IBF_OK;
 }
 
@@ -280,10 +290,11 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     for (int g = 0; g < ngrids; ++g) total_cols += x_modes(grids[g]);
 
     long long spec = 0, cells = 0;
-    int zoff = 0, poff = 0, xblk = 0, yzblk = 0, strblk = 0, slabblk = 0;
-    std::vector<int> str_start(ngrids + 1, 0), slab_start(ngrids + 1, 0);
+    int zoff = 0, poff = 0, xblk = 0, yzblk = 0, strblk = 0, slabblk = 0, yfftblk = 0, sweepblk = 0;
+    std::vector<int> str_start(ngrids + 1, 0), slab_start(ngrids + 1, 0), yfft_start(ngrids + 1, 0),
+        sweep_start(ngrids + 1, 0);
     std::vector<double> twx_all, twy_all, tmp;
-    size_t maxx = 0, maxyz = 0, maxslab = 0;
+    size_t maxx = 0, maxyz = 0, maxslab = 0, maxyfft = 0;
     for (int g = 0; g < ngrids; ++g) {
         GridHost &H = pl->grids[g];
         H.g = grids[g];
@@ -339,8 +350,16 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         yzblk += d.ncb;
         str_start[g] = strblk;
         slab_start[g] = slabblk;
-        if (d.yzk == 0) strblk += d.ncb;
-        else slabblk += d.ncb;
+        yfft_start[g] = yfftblk;
+        sweep_start[g] = sweepblk;
+        if (d.yzk == 0) {
+            strblk += d.ncb;
+        } else if (d.yzk == 1) {
+            slabblk += d.ncb;
+        } else {
+            yfftblk += d.nz * d.ncb;
+            sweepblk += (int)(((long long)d.ncb * d.ny * d.mb + kSweepThreads - 1) / kSweepThreads);
+        }
         d.dx = H.g.lx / d.nx; d.dy = H.g.ly / d.ny;
         d.rdx = 1.0 / d.dx; d.rdy = 1.0 / d.dy;
         d.inv_nxy = 1.0 / ((double)d.nx * d.ny);
@@ -358,15 +377,21 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
             maxx = std::max(maxx, n.x);
             maxyz = std::max(maxyz, n.yz);
             maxslab = std::max(maxslab, n.slab);
+            maxyfft = std::max(maxyfft, n.yfft);
         }
         pl->maxnz = std::max(pl->maxnz, d.nz);
         pl->total_cells += (long long)d.nx * d.ny * d.nz;
     }
     const size_t cap = smem_cap(prop);
-    if (maxx > cap || maxyz > cap || maxslab > cap || (size_t)10 * (pl->maxnz + 1) * 8 > cap)
+    if (maxx > cap || maxyz > cap || maxslab > cap || maxyfft > cap || (size_t)10 * (pl->maxnz + 1) * 8 > cap)
         return IBF_ERR_UNSUPPORTED_SIZE;
     str_start[ngrids] = strblk;
     slab_start[ngrids] = slabblk;
+    yfft_start[ngrids] = yfftblk;
+    sweep_start[ngrids] = sweepblk;
+    pl->yfftsmem = maxyfft;
+    pl->nyfftblk = yfftblk;
+    pl->nsweepblk = sweepblk;
     pl->xsmem = maxx;
     pl->yzsmem = maxyz;
     pl->slabsmem = maxslab;
@@ -420,11 +445,15 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     GridDev *dgrids;
     IBF_TRY(dalloc(pl, &dgrids, sizeof(GridDev) * ngrids));
     w.grids = dgrids;
-    int *dx, *dyz, *dstr, *dslab;
+    int *dx, *dyz, *dstr, *dslab, *dyfft, *dsweep;
     IBF_TRY(dalloc(pl, &dx, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dyz, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dstr, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dslab, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(dalloc(pl, &dyfft, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(dalloc(pl, &dsweep, sizeof(int) * (ngrids + 1)));
+    w.yfft_start = dyfft;
+    w.sweep_start = dsweep;
     w.xblk_start = dx;
     w.yzblk_start = dyz;
     w.ystr_start = dstr;
@@ -447,6 +476,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     IBF_TRY(dalloc(pl, &twy, csz * twy_all.size() / 2));
     w.twx = twx;
     w.twy = twy;
+    if (!mixed && pl->opts.pressure == IBF_P_IMPLICIT) IBF_TRY(dalloc(pl, &w.bws, sizeof(double) * (size_t)cells));
     if (mixed) {
         IBF_TRY(dalloc(pl, &w.bdf, sizeof(float2) * (size_t)cells));
         IBF_TRY(dalloc(pl, &w.phi_hi, sizeof(float) * (size_t)cells));
@@ -475,6 +505,8 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     IBF_TRY(upload(ys.data(), dyz, sizeof(int) * (ngrids + 1)));
     IBF_TRY(upload(str_start.data(), dstr, sizeof(int) * (ngrids + 1)));
     IBF_TRY(upload(slab_start.data(), dslab, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(upload(yfft_start.data(), dyfft, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(upload(sweep_start.data(), dsweep, sizeof(int) * (ngrids + 1)));
     IBF_TRY(upload(hz.data(), w.z.hz, sizeof(double) * nzt));
     IBF_TRY(upload(rhz.data(), w.z.rhz, sizeof(double) * nzt));
     IBF_TRY(upload(rgzf.data(), w.z.rgzf, sizeof(double) * nzt));
@@ -580,9 +612,17 @@ ibf_status solve_core(Ctx &c, int first) {
     const Work &w = pl->work;
     if (pl->nstrblk > 0)
         IBF_TRY(timed(c, "yz_forward", [&]() { return launch_yzfwd(pl->mixed, w, pl->nstrblk, pl->yzsmem, c.st); }));
+    if (pl->nyfftblk > 0) {
+        IBF_TRY(timed(c, "y_fft_forward", [&]() { return launch_yfft(pl->mixed, 0, w, pl->nyfftblk, pl->yfftsmem, c.st); }));
+        IBF_TRY(timed(c, "z_sweep_forward", [&]() { return launch_zsweep(pl->mixed, 0, w, pl->nsweepblk, c.st); }));
+    }
     IBF_TRY(timed(c, "mode00", [&]() { return launch_k00(w, pl->mixed, first, pl->maxnz, c.st); }));
     if (pl->nstrblk > 0)
         IBF_TRY(timed(c, "yz_backward", [&]() { return launch_yzbwd(pl->mixed, w, pl->nstrblk, pl->yzsmem, c.st); }));
+    if (pl->nyfftblk > 0) {
+        IBF_TRY(timed(c, "z_sweep_backward", [&]() { return launch_zsweep(pl->mixed, 1, w, pl->nsweepblk, c.st); }));
+        IBF_TRY(timed(c, "y_fft_inverse", [&]() { return launch_yfft(pl->mixed, 1, w, pl->nyfftblk, pl->yfftsmem, c.st); }));
+    }
     if (pl->nslabblk > 0)
         IBF_TRY(timed(c, "yz_slab", [&]() { return launch_yzslab(pl->mixed, w, pl->nslabblk, pl->slabsmem, c.st); }));
     return IBF_OK;
@@ -594,9 +634,12 @@ ibf_status run(ibf_plan *pl, const ibf_fields *in, const ibf_fields *out, double
     const Work &w = pl->work;
     const double s = alpha * dt, rs = 1.0 / s;
     const int mixed = pl->mixed;
-    // fp64 path: the adjoint's phi lives in the plan (no phi output); mixed path: phi is
-    // refined as float-float in the plan and written out by the correction kernel.
-    const int use_ws = adjoint ? 1 : 0;
+    // fp64 path: the adjoint's phi, and phi under a pressure update, live in the plan;
+    // mixed path: phi is refined as float-float in the plan and written out by the
+    // correction kernel.
+    const int pmode = adjoint ? 0 : pl->opts.pressure;
+    const int use_ws = (adjoint || pmode) ? 1 : 0;
+    const double cimp = pmode == IBF_P_IMPLICIT ? 0.5 * alpha * dt * pl->opts.inv_re : 0.0;
     const int R = mixed ? pl->opts.refine_steps : 0;
     cudaError_t e = cudaMemsetAsync(w.maxb, 0, sizeof(unsigned long long) * pl->ngrids, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.maxdiv, 0, sizeof(unsigned long long) * pl->ngrids, st);
@@ -620,7 +663,7 @@ ibf_status run(ibf_plan *pl, const ibf_fields *in, const ibf_fields *out, double
         }));
     }
     IBF_TRY(for_chunks(c, adjoint ? "correct_adjoint" : "correct", in, out, [&](const UserPtrs &p, int nb) {
-        return launch_correct(mixed, adjoint, w, p, use_ws, R > 0, nb, s, st);
+        return launch_correct(mixed, adjoint, w, p, use_ws, R > 0, nb, s, pmode, cimp, st);
     }));
     if (!adjoint && stats && (stats->max_div || stats->max_div_in || stats->compat)) {
         if (stats->max_div) {
@@ -748,8 +791,12 @@ ibf_status tune_grid(const ibf_grid &g, const ibf_opts &opts, int device, ibf_tu
 
     ibf_tuning best = forced;
     float tbest = -1.f;
+    static const bool log = getenv("IBF_AUTOTUNE_LOG") != nullptr;  // print every timed candidate
     auto consider = [&](ibf_tuning cand) {
         const float ms = time_shape(b, cand);
+        if (log)
+            fprintf(stderr, "ibf autotune %dx%dx%d: rows %d x_n1 %d y_n1 %d yz_kernel %d mb %d tri %d -> %.4f ms\n",
+                    g.nx, g.ny, g.nz, cand.rows, cand.x_n1, cand.y_n1, cand.yz_kernel, cand.mb, cand.tri, ms);
         if (ms > 0.f && (tbest < 0.f || ms < tbest)) { tbest = ms; best = cand; }
     };
     if (status == IBF_OK) {
@@ -775,15 +822,16 @@ ibf_status tune_grid(const ibf_grid &g, const ibf_opts &opts, int device, ibf_tu
                     if (n1 != best.y_n1 && fft_pair_ok(g.ny, n1)) { ibf_tuning c2 = best; c2.y_n1 = n1; consider(c2); }
             const ibf_tuning base = best;
             const int nxh = x_modes(g);
-            for (int kern = 1; kern <= 2; ++kern) {
+            for (int kern = 1; kern <= 3; ++kern) {
                 if (forced.yz_kernel > 0 && forced.yz_kernel != kern) continue;
                 for (int mb : kMb) {
                     if (mb > nxh && mb != 1) continue;
                     if (forced.mb > 0 && forced.mb != mb) continue;
-                    const int ntri = kern == 1 ? 1 : 2 + ilog2_floor(g.nz);
+                    // slab: Thomas, 1-2 reduction levels, full reduction
+                    const int ntri = kern == 2 ? 1 + ilog2_floor(g.nz) : 1;
                     for (int tri = 1; tri <= ntri; ++tri) {
                         if (forced.tri > 0 && forced.tri != tri) continue;
-                        if (kern == 2 && tri > 3 && tri != ntri) continue;  // Thomas, 1-2 levels, full reduction
+                        if (kern == 2 && tri > 3 && tri != ntri) continue;
                         ibf_tuning c2 = base;
                         c2.yz_kernel = kern;
                         c2.mb = mb;
@@ -844,7 +892,10 @@ ibf_status ibf_projection_plan_tuned(ibf_plan **plan, const ibf_grid *grids, int
     *plan = nullptr;
     if (!grids || !opts || ngrids < 1 || ngrids > IBF_MAX_GRIDS || device < 0) return IBF_ERR_INVALID_ARG;
     if (opts->precision != IBF_FP64 && opts->precision != IBF_MIXED) return IBF_ERR_INVALID_ARG;
-    if (opts->refine_steps < 0 || opts->refine_steps > 8 || opts->reserved != 0) return IBF_ERR_INVALID_ARG;
+    if (opts->refine_steps < 0 || opts->refine_steps > 8) return IBF_ERR_INVALID_ARG;
+    if (opts->pressure < IBF_P_PHI || opts->pressure > IBF_P_IMPLICIT || !std::isfinite(opts->inv_re) ||
+        opts->inv_re < 0)
+        return IBF_ERR_INVALID_ARG;
     if (opts->precision == IBF_FP64 && opts->refine_steps != 0) return IBF_ERR_INVALID_ARG;
     // host-side validation of every grid before touching the device
     for (int g = 0; g < ngrids; ++g) {
@@ -853,7 +904,7 @@ ibf_status ibf_projection_plan_tuned(ibf_plan **plan, const ibf_grid *grids, int
         if (s != IBF_OK) return s;
         if (tuning) {
             const ibf_tuning &t = tuning[g];
-            if (t.yz_kernel > 2 || (t.rows > 0 && (t.rows & 1))) return IBF_ERR_INVALID_ARG;
+            if (t.yz_kernel > 3 || (t.rows > 0 && (t.rows & 1))) return IBF_ERR_INVALID_ARG;
         }
     }
     cudaError_t e = cudaSetDevice(device);
@@ -872,7 +923,8 @@ ibf_status ibf_plan_get_tuning(const ibf_plan *plan, int g, ibf_tuning *out) {
 
 ibf_status ibf_project(ibf_plan *plan, const ibf_fields *in, const ibf_fields *out, double dt, double alpha,
                        const ibf_stats *stats, void *stream) {
-    if (!plan || !fields_ok(in, plan->ngrids, false) || !fields_ok(out, plan->ngrids, true)) return IBF_ERR_INVALID_ARG;
+    if (!plan || !fields_ok(in, plan->ngrids, plan->opts.pressure != IBF_P_PHI) || !fields_ok(out, plan->ngrids, true))
+        return IBF_ERR_INVALID_ARG;
     if (!(dt > 0) || !(alpha > 0) || !std::isfinite(dt) || !std::isfinite(alpha)) return IBF_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(plan->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");

@@ -13,6 +13,7 @@ constexpr int kXThreads = 256;   // x-direction (row) kernels and stencil kernel
 constexpr int kYZThreads = 128;  // y-FFT + z-tridiagonal column kernels
 constexpr int kYZStages = 2;     // planes in flight per column block in the yz kernels
 constexpr int kSlabThreads = 256;  // resident-slab y/z kernel
+constexpr int kSweepThreads = 256; // split y/z path: Thomas sweeps, one thread per mode
 
 // Division by a run-time invariant d (Granlund & Montgomery, PLDI 1994, round-up
 // variant): n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31.
@@ -26,7 +27,8 @@ struct GridDev {
     int wall_x, wall_y;        // 1: that direction is wall-bounded (Neumann phi, DCT-II transform)
     int nxu, nyv;              // faces of u per row (nx + wall_x), rows of v per plane (ny + wall_y)
     int dctx_off, dcty_off;    // offsets of the exp(-i pi m/(2N)) tables of the DCTs (in twx / twy)
-    int yzk;                   // y/z kernel: 0 streaming (k_yzfwd + k_yzbwd), 1 resident slab (k_yzslab)
+    int yzk;                   // y/z kernels: 0 streaming (k_yzfwd + k_yzbwd), 1 resident slab (k_yzslab),
+                               // 2 split (k_yfft, k_zsweep_fwd / k_zsweep_bwd)
     int cr_levels;             // slab kernel: cyclic-reduction levels before Thomas (0: Thomas with the table)
     int nx1, nx2, ny1, ny2;    // two-level FFT factors: nx = nx1*nx2, ny = ny1*ny2
     int mb, ncb;               // x-modes per column block of the yz kernels, number of blocks
@@ -64,13 +66,16 @@ struct Work {
     const int *yzblk_start;    // prefix of column blocks over all grids [ngrids+1] (pivot table)
     const int *ystr_start;     // prefix of column blocks over grids with streaming y/z kernels
     const int *slab_start;     // prefix of column blocks over grids with the resident-slab kernel
+    const int *yfft_start;     // split path: prefix of (plane, column block) FFT blocks over grids
+    const int *sweep_start;    // split path: prefix of Thomas-sweep blocks (kSweepThreads modes each)
     double *sol00;             // per level (z_off + k): solution of the (0,0) mode, written by k_00
     ZArrays z;
     void *spec;                // complex<T> spectrum, per grid nz*ncb*ny*mb
     void *tab;                 // T pivot table, same layout as spec (real entries)
     const void *twx, *twy;     // complex<T> twiddle tables
     float2 *bdf;               // float-float right-hand side (mixed path) per cell
-    double *phi_ws;            // per-cell fp64 phi of the adjoint solve (fp64 path)
+    double *phi_ws;            // per-cell fp64 phi of the adjoint solve / of a pressure update (fp64 path)
+    double *bws;               // per-cell fp64 right-hand side (fp64 path with the implicit pressure update)
     float *phi_hi, *phi_lo;    // per-cell float-float phi being refined (mixed path)
     double *partial;           // per (grid, k, row block) plane sums of the right-hand side
     double *partial_phi;       // per (grid, k, row block) plane sums of the current phi (refinement)
@@ -98,10 +103,12 @@ cudaError_t launch_yzfwd(int mixed, const Work &w, int nblk, size_t smem, cudaSt
 cudaError_t launch_yzbwd(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cudaStream_t st);
 cudaError_t launch_yzslab(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
+cudaError_t launch_yfft(int mixed, int inverse, const Work &w, int nblk, size_t smem, cudaStream_t st);
+cudaError_t launch_zsweep(int mixed, int backward, const Work &w, int nblk, cudaStream_t st);
 cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
                         size_t smem, cudaStream_t st);
 cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
-                           int nblk, double s, cudaStream_t st);
+                           int nblk, double s, int pmode, double cimp, cudaStream_t st);
 cudaError_t launch_divstat(int mixed, const Work &w, const UserPtrs &p, int nblk, cudaStream_t st);
 cudaError_t launch_finalize(const Work &w, double *max_div, double *max_div_in, double *compat, double s,
                             cudaStream_t st);

@@ -165,8 +165,10 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                         have_v = true;
                         if (act) {
                             if (MODE == XM_DIV) vmax = fmaxf(vmax, absv<A>(bv));
-                            if (sizeof(T) == 4)
+                            if constexpr (sizeof(T) == 4)
                                 w.bdf[G.cell_off + pbase + row + i] = *reinterpret_cast<const float2 *>(&bv);
+                            else if (MODE == XM_DIV && w.bws)
+                                w.bws[G.cell_off + pbase + row + i] = *reinterpret_cast<const double *>(&bv);
                             acc = A::add(acc, bv);
                             val = to_T<T, A>(bv) * scale;
                         }
@@ -393,8 +395,10 @@ constexpr int kRowGroupC = 2;
 //                    mixed path: also writes phi (fp64) from its float-float value.
 // adjoint (ADJ = 1): g* = g_u + hz_k rdx (psi_{i-1} - psi_i), ...,
 //                    w_k = g_w,k + psi_{k-1} [k>=1] - psi_k [k<=nz-1].
-template <class A, int ADJ, bool W>
-__global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, int use_ws, int lo_valid, double s) {
+// PU: forward with a pressure update (pmode 1: p_n + phi, 2: minus cimp (b - <b>)).
+template <class A, int ADJ, bool W, bool PU>
+__global__ void __launch_bounds__(kXThreads, 4)
+    k_correct(Work w, UserPtrs p, int use_ws, int lo_valid, double s, int pmode, double cimp) {
     typedef typename A::V V;
     const int b = blockIdx.x + p.blk0;
     const int g = find_grid(w.xblk_start, w.ngrids, b);
@@ -421,7 +425,11 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
     const ptrdiff_t ubase = (ptrdiff_t)k * ny * nxu, vbase = (ptrdiff_t)k * (W ? G.nyv : ny) * nx;
     const double *ui = p.in_u[gi] + ubase, *vi = p.in_v[gi] + vbase, *wi = p.in_w[gi] + pbase;
     double *uo = p.out_u[gi] + ubase, *vo = p.out_v[gi] + vbase, *wo = p.out_w[gi] + pbase;
-    double *po = (MIX && !ADJ) ? p.out_p[gi] + pbase : nullptr;
+    // pressure output (forward): phi (mixed path; the fp64 path's phi is already in out.p),
+    // or p_n + phi [- cimp (b - <b>)] (Eq. pressure) with p_n = in.p
+    double *po = (!ADJ && (MIX || PU)) ? p.out_p[gi] + pbase : nullptr;
+    const double *pn = (!ADJ && PU) ? p.in_p[gi] + pbase : nullptr;
+    const double mean_b = w.mean_b[g];
     V cu, cv, cw;
     if (ADJ) {
         const double hz = w.z.hz[zo + k];
@@ -495,7 +503,24 @@ __global__ void __launch_bounds__(kXThreads, 4) k_correct(Work w, UserPtrs p, in
                         if (k == 0) wo[c] = rw[q];
                         else wo[c] = rw[q] + A::store(A::mul(cw, A::sub(pkm[q], Pc)));
                         if (k == nz - 1) wo[c + plane] = rwt[q];
-                        if (po) po[c] = A::store(A::norm(Pc));
+                        if (po) {
+                            if constexpr (!PU) {
+                                po[c] = A::store(A::norm(Pc));
+                            } else {
+                                double pv = pn[c] + A::store(A::norm(Pc));
+                                if (pmode == 2) {
+                                    double bb;
+                                    if constexpr (MIX) {
+                                        const float2 bd = w.bdf[G.cell_off + pbase + c];
+                                        bb = df_to_f64(df_sub(df{bd.x, bd.y}, Coef<A>::c(mean_b)));
+                                    } else {
+                                        bb = w.bws[G.cell_off + pbase + c] - mean_b;
+                                    }
+                                    pv -= cimp * bb;
+                                }
+                                po[c] = pv;
+                            }
+                        }
                     }
                 }
                 Pjm = Pc;
@@ -620,22 +645,25 @@ cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, i
 
 template <bool W>
 cudaError_t launch_correct_w(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
-                             int nblk, double s, cudaStream_t st) {
+                             int nblk, double s, int pm, double ci, cudaStream_t st) {
+    const dim3 gr = grid1(nblk);
     if (mixed) {
-        if (adjoint) k_correct<DFArith, 1, W><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
-        else k_correct<DFArith, 0, W><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
+        if (adjoint) k_correct<DFArith, 1, W, false><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, 0, 0.0);
+        else if (pm) k_correct<DFArith, 0, W, true><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, pm, ci);
+        else k_correct<DFArith, 0, W, false><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, 0, 0.0);
     } else {
-        if (adjoint) k_correct<F64Arith, 1, W><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
-        else k_correct<F64Arith, 0, W><<<grid1(nblk), kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s);
+        if (adjoint) k_correct<F64Arith, 1, W, false><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, 0, 0.0);
+        else if (pm) k_correct<F64Arith, 0, W, true><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, pm, ci);
+        else k_correct<F64Arith, 0, W, false><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, 0, 0.0);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
-                           int nblk, double s, cudaStream_t st) {
+                           int nblk, double s, int pmode, double cimp, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
-    return w.walls ? launch_correct_w<true>(mixed, adjoint, w, p, use_ws, lo_valid, nblk, s, st)
-                   : launch_correct_w<false>(mixed, adjoint, w, p, use_ws, lo_valid, nblk, s, st);
+    return w.walls ? launch_correct_w<true>(mixed, adjoint, w, p, use_ws, lo_valid, nblk, s, pmode, cimp, st)
+                   : launch_correct_w<false>(mixed, adjoint, w, p, use_ws, lo_valid, nblk, s, pmode, cimp, st);
 }
 
 cudaError_t launch_divstat(int mixed, const Work &w, const UserPtrs &p, int nblk, cudaStream_t st) {

@@ -101,7 +101,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     if (!in->u || !in->v || !in->w || !out->u || !out->v || !out->w || !out->p) return IBF_ERR_INVALID_ARG;
     if (!(dt > 0) || !(alpha > 0) || !std::isfinite(dt) || !std::isfinite(alpha)) return IBF_ERR_INVALID_ARG;
     if (opts->precision != IBF_FP64 && opts->precision != IBF_MIXED) return IBF_ERR_INVALID_ARG;
-    if (opts->refine_steps < 0 || opts->refine_steps > 8 || opts->reserved != 0) return IBF_ERR_INVALID_ARG;
+    if (opts->refine_steps < 0 || opts->refine_steps > 8 || opts->pressure != IBF_P_PHI) return IBF_ERR_INVALID_ARG;
     if (opts->precision == IBF_FP64 && opts->refine_steps != 0) return IBF_ERR_INVALID_ARG;
     const ibf_grid &g = *grid;
     if (g.nx < 1 || g.ny < 1 || g.nz < 1 || !(g.lx > 0) || !(g.ly > 0) || !(g.lz > 0)) return IBF_ERR_INVALID_ARG;
@@ -252,6 +252,8 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     w.yzblk_start = reinterpret_cast<const int *>(base + o_ys);
     w.ystr_start = w.yzblk_start;
     w.slab_start = reinterpret_cast<const int *>(base + o_slab);
+    w.yfft_start = w.slab_start;  // no split-path blocks either
+    w.sweep_start = w.slab_start;
     w.sol00 = reinterpret_cast<double *>(base + o_sol00);
     w.z.hz = reinterpret_cast<double *>(base + o_hz);
     w.z.rhz = reinterpret_cast<double *>(base + o_rhz);
@@ -304,7 +306,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
         if (e == cudaSuccess) e = solve(0);
         if (e == cudaSuccess) e = launch_xinv(mixed, IM_ACCUM, w, p, 0, r > 0, nxblk, xsmem, st);
     }
-    if (e == cudaSuccess) e = launch_correct(mixed, 0, w, p, 0, R > 0, nxblk, sc, st);
+    if (e == cudaSuccess) e = launch_correct(mixed, 0, w, p, 0, R > 0, nxblk, sc, IBF_P_PHI, 0.0, st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return IBF_ERR_CUDA;

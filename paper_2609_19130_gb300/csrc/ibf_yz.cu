@@ -421,6 +421,86 @@ __global__ void __launch_bounds__(kSlabThreads) k_yzslab(Work w) {
     }
 }
 
+// ================================================================ split y/z path
+// y transform of one (plane, column block): the spectrum chunk of ny*mb x-modes is
+// loaded, transformed along y (FFT, or DCT-II / DCT-III input stage in a wall-bounded
+// y) and written back in place, in slot order (forward) or row order (inverse).
+// Every (plane, block) is independent, so the launch has nz*ncb blocks per grid.
+template <typename T, int DIR, bool W>
+__global__ void __launch_bounds__(kYZThreads) k_yfft(Work w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = find_grid(w.yfft_start, w.ngrids, blockIdx.x);
+    const GridDev &G = w.grids[g];
+    const int lb = blockIdx.x - __ldg(w.yfft_start + g);
+    const int ncb = G.ncb, k = lb / ncb, cb = lb - k * ncb;
+    const int ny = G.ny, mb = G.mb, nxh = G.nxh;
+    const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
+    const int nslot = ny * mb;
+    const int nvalid = min(mb, nxh - cb * mb);
+    const int wall_y = W ? G.wall_y : 0;
+    const cx<T> *twy = reinterpret_cast<const cx<T> *>(w.twy) + G.twy_off;
+    const cx<T> *dcty = reinterpret_cast<const cx<T> *>(w.twy) + G.dcty_off;
+    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *pl = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + ((size_t)k * ncb + cb) * nslot;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int t = tid; t < nslot; t += nthr) {
+        const int r = (int)fdiv((unsigned)t, fmb), mm = t - r * mb;
+        // forward: row r of the x-spectrum; inverse: slot r (FFT output order)
+        const int pos = DIR < 0 ? pos_nat(wall_y ? dct_perm(r, ny) : r, fN2) : pos_nat(r, fN2);
+        buf[mm * sstride + pos] = (mm < nvalid) ? pl[t] : cx<T>{(T)0, (T)0};
+    }
+    __syncthreads();
+    if (DIR > 0 && wall_y) dct_pre<T>(buf, mb, sstride, ny, N1, N2, fN1, dcty);
+    fft_batch<T, DIR>(buf, mb, sstride, N1, N2, fN1, fN2, twy);
+    if (DIR < 0 && wall_y) dct_post<T>(buf, mb, sstride, ny, N1, N2, fN1, dcty);
+    for (int t = tid; t < nslot; t += nthr) {
+        const int r = (int)fdiv((unsigned)t, fmb), mm = t - r * mb;
+        const int pos = DIR < 0 ? pos_nat(r, fN2) : pos_nat(wall_y ? dct_perm(r, ny) : r, fN2);
+        if (mm < nvalid) pl[t] = buf[mm * sstride + pos];
+    }
+}
+
+// Thomas sweeps of the split path: one thread per mode of a grid (slot gs of the
+// flattened [column block][slot] index, so plane k of the spectrum is one contiguous
+// run of ncb*nslot modes), pivots from the plan's table.  Forward overwrites the
+// spectrum with d'; the (0,0) mode passes through (k_00 solves it); backward turns
+// d' into phi_hat.
+template <typename T, bool BWD>
+__global__ void __launch_bounds__(kSweepThreads) k_zsweep(Work w) {
+    const int g = find_grid(w.sweep_start, w.ngrids, blockIdx.x);
+    const GridDev &G = w.grids[g];
+    const int gs = (blockIdx.x - __ldg(w.sweep_start + g)) * kSweepThreads + threadIdx.x;
+    const int nslot = G.ny * G.mb, M = G.ncb * nslot, nz = G.nz;
+    if (gs >= M) return;
+    const int cb = gs / nslot, q = gs - cb * nslot;
+    const int mm = q - (int)fdiv((unsigned)q, G.fmb) * G.mb;
+    if (cb * G.mb + mm >= G.nxh) return;  // padding column of the last block
+    const bool singular = gs == 0;
+    cx<T> *sp = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + gs;
+    const T *tb = reinterpret_cast<const T *>(w.tab) + G.tab_off + gs;
+    const T *a = zarr<T>(w.z.az, w.z.azf) + G.z_off;
+    const T *c = zarr<T>(w.z.cz, w.z.czf) + G.z_off;
+    cx<T> s = {(T)0, (T)0};
+    if (!BWD) {
+#pragma unroll 8
+        for (int k = 0; k < nz; ++k) {
+            const cx<T> r = sp[(size_t)k * M];
+            const T inv = tb[(size_t)k * M], ak = a[k];
+            s = singular ? r : cx<T>{(r.x - ak * s.x) * inv, (r.y - ak * s.y) * inv};
+            sp[(size_t)k * M] = s;
+        }
+    } else {
+#pragma unroll 8
+        for (int k = nz - 1; k >= 0; --k) {
+            const cx<T> d = sp[(size_t)k * M];
+            const T cp = c[k] * tb[(size_t)k * M];
+            s = singular ? d : cx<T>{d.x - cp * s.x, d.y - cp * s.y};
+            sp[(size_t)k * M] = s;
+        }
+    }
+}
+
 // ================================================================ k_00 (fp64, one CTA per grid)
 template <typename T>
 __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
@@ -520,9 +600,9 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     const size_t stride = (size_t)G.ncb * G.ny * G.mb;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         const double v = rhs[k] - mphi;
-        // streaming kernels: slot (0,0) of the y-transformed spectrum; the slab kernel
-        // (whose spectrum is still untransformed in y here) reads sol00
-        if (G.yzk == 0) spec[(size_t)k * stride] = {(T)v, (T)0};
+        // streaming and split paths: slot (0,0) of the y-transformed spectrum; the slab
+        // kernel (whose spectrum is still untransformed in y here) reads sol00
+        if (G.yzk != 1) spec[(size_t)k * stride] = {(T)v, (T)0};
         w.sol00[zo + k] = v;
     }
 }
@@ -604,6 +684,42 @@ cudaError_t launch_yzslab(int mixed, const Work &w, int nblk, size_t smem, cudaS
     return cudaGetLastError();
 }
 
+cudaError_t launch_yfft(int mixed, int inverse, const Work &w, int nblk, size_t smem, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    const dim3 gr = grid1(nblk);
+    if (mixed) {
+        if (inverse) {
+            if (w.walls) k_yfft<float, 1, true><<<gr, kYZThreads, smem, st>>>(w);
+            else k_yfft<float, 1, false><<<gr, kYZThreads, smem, st>>>(w);
+        } else {
+            if (w.walls) k_yfft<float, -1, true><<<gr, kYZThreads, smem, st>>>(w);
+            else k_yfft<float, -1, false><<<gr, kYZThreads, smem, st>>>(w);
+        }
+    } else {
+        if (inverse) {
+            if (w.walls) k_yfft<double, 1, true><<<gr, kYZThreads, smem, st>>>(w);
+            else k_yfft<double, 1, false><<<gr, kYZThreads, smem, st>>>(w);
+        } else {
+            if (w.walls) k_yfft<double, -1, true><<<gr, kYZThreads, smem, st>>>(w);
+            else k_yfft<double, -1, false><<<gr, kYZThreads, smem, st>>>(w);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zsweep(int mixed, int backward, const Work &w, int nblk, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    const dim3 gr = grid1(nblk);
+    if (mixed) {
+        if (backward) k_zsweep<float, true><<<gr, kSweepThreads, 0, st>>>(w);
+        else k_zsweep<float, false><<<gr, kSweepThreads, 0, st>>>(w);
+    } else {
+        if (backward) k_zsweep<double, true><<<gr, kSweepThreads, 0, st>>>(w);
+        else k_zsweep<double, false><<<gr, kSweepThreads, 0, st>>>(w);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t st) {
     if (mixed) k_build_table<float><<<grid1(nblk), 256, 0, st>>>(w);
     else k_build_table<double><<<grid1(nblk), 256, 0, st>>>(w);
@@ -621,10 +737,14 @@ cudaError_t set_smem_limits_yz(int mixed) {
             set((const void *)k_yzfwd<float, W>);
             set((const void *)k_yzbwd<float, W>);
             set((const void *)k_yzslab<float, W>);
+            set((const void *)k_yfft<float, -1, W>);
+            set((const void *)k_yfft<float, 1, W>);
         } else {
             set((const void *)k_yzfwd<double, W>);
             set((const void *)k_yzbwd<double, W>);
             set((const void *)k_yzslab<double, W>);
+            set((const void *)k_yfft<double, -1, W>);
+            set((const void *)k_yfft<double, 1, W>);
         }
     };
     set_all(std::false_type{});

@@ -46,7 +46,7 @@ def _plan(grid_kw, opts_kw=None, n=1):
     arr = (N.ibf_grid * n)()
     for i in range(n):
         arr[i] = N.ibf_grid(**g)
-    o = dict(precision=1, refine_steps=1, autotune=0, reserved=0)
+    o = dict(precision=1, refine_steps=1, autotune=0, pressure=0, inv_re=0.0)
     o.update(opts_kw or {})
     h = C.c_void_p()
     st = N.lib().ibf_projection_plan(C.byref(h), arr, n, C.byref(N.ibf_opts(**o)), 0)
@@ -84,7 +84,8 @@ def test_explicit_faces_validation(lib):
 
 
 @pytest.mark.parametrize("okw", [dict(precision=3), dict(refine_steps=-1), dict(refine_steps=9),
-                                 dict(precision=0, refine_steps=1), dict(reserved=1)])
+                                 dict(precision=0, refine_steps=1), dict(pressure=3),
+                                 dict(pressure=2, inv_re=-1.0), dict(inv_re=float('nan'))])
 def test_opts_validation(lib, okw):
     st, h = _plan({}, okw)
     assert st == N.IBF_ERR_INVALID_ARG
@@ -111,7 +112,7 @@ def test_valid_plan_without_gpu_reports_cuda_error(lib):
     assert N.last_error()
 
 
-@pytest.mark.parametrize("bad", [dict(rows=3), dict(yz_kernel=3)])
+@pytest.mark.parametrize("bad", [dict(rows=3), dict(yz_kernel=4)])
 def test_tuning_validation_on_host(lib, bad):
     """Forced launch shapes are checked on the host before the device is touched."""
     g = (N.ibf_grid * 1)()
@@ -119,6 +120,6 @@ def test_tuning_validation_on_host(lib, bad):
     t = (N.ibf_tuning * 1)()
     t[0] = N.ibf_tuning(*(bad.get(f, 0) for f in N.TUNING_FIELDS))
     h = C.c_void_p()
-    o = N.ibf_opts(1, 1, 0, 0)
+    o = N.ibf_opts(1, 1, 0, 0, 0.0)
     assert N.lib().ibf_projection_plan_tuned(C.byref(h), g, 1, C.byref(o), 0, t) == N.IBF_ERR_INVALID_ARG
     assert not h.value

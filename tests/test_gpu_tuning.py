@@ -63,6 +63,7 @@ VARIANTS = [
     dict(yz_kernel=2, mb=2, tri=3), dict(yz_kernel=2, mb=4, tri=0),   # tri 0: default (Thomas + table)
     dict(yz_kernel=2, mb=1, tri=99),                                   # replaced by full reduction below
     dict(rows=2), dict(rows=6), dict(x_n1=2, y_n1=2), dict(x_n1=4, y_n1=4),
+    dict(yz_kernel=3, mb=1), dict(yz_kernel=3, mb=4), dict(yz_kernel=3, mb=2, y_n1=2),
 ]
 
 
@@ -96,7 +97,8 @@ def test_forced_variants_match_oracle(gdesc, prec):
         (ug, vg, wg, pg), st, used = project(g, prec, [var], u, v, w)
         for k, val in var.items():
             if val > 0:
-                assert used[k] == (min(val, nx // 2 + 1 if not wx else nx) if k == "mb" else val), (k, used)
+                want = {"mb": min(val, nx // 2 + 1 if not wx else nx)}.get(k, val)
+                assert used[k] == want, (k, used)
         assert rel_l2(pg, phi_o) <= TOL[prec], (var, rel_l2(pg, phi_o))
         for a, b in ((ug, u_o), (vg, v_o), (wg, w_o)):
             assert np.abs(a - b).max() <= 10 * TOL[prec] * umax, (var, np.abs(a - b).max())
@@ -108,7 +110,7 @@ def test_invalid_tunings_rejected():
     g = Grid(24, 16, 8, 1.0, 1.0, 1.0, beta=1.0)
     for bad, status in ((dict(x_n1=5), N.IBF_ERR_UNSUPPORTED_SIZE),     # 5 does not divide 24
                         (dict(tri=9), N.IBF_ERR_INVALID_ARG),           # > 1 + log2(8)
-                        (dict(yz_kernel=3), N.IBF_ERR_INVALID_ARG),
+                        (dict(yz_kernel=4), N.IBF_ERR_INVALID_ARG),
                         (dict(rows=3), N.IBF_ERR_INVALID_ARG)):         # rows must be even
         with pytest.raises(IBFError) as ei:
             Plan([g], precision=MIXED, tuning=[bad])

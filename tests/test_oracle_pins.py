@@ -277,3 +277,26 @@ def test_tanh_faces_properties():
     z0 = O.zfaces_tanh(64, 1.0, 0.0)
     z1 = O.zfaces_tanh(64, 1.0, 1e-6)
     assert np.max(np.abs(z1 - np.arange(65) / 64)) < 1e-10 and np.max(np.abs(z0 - np.arange(65) / 64)) < 1e-15
+
+
+# ---------------------------------------------------------------- Eq. (pressure)
+@pytest.mark.parametrize("walls", [(False, False), (True, True)])
+def test_pressure_update_closed_form(walls):
+    """p_{n+1} = p_n + phi - alpha dt/(2 Re) lap(phi): for a discrete eigenfunction phi
+    (eigenvalue lam, uniform z) this is p_n + (1 - alpha dt lam/(2 Re)) phi exactly, and
+    with inv_re = 0 it is p_n + phi."""
+    nx, ny, nz, a, b, c = 12, 16, 8, 3, 2, 1
+    lx, ly, lz = 1.1, 0.8, 1.5
+    g = O.Grid(nx, ny, nz, lx=lx, ly=ly, lz=lz, beta=0.0, wall_x=walls[0], wall_y=walls[1])
+    i, j, k = np.arange(nx), np.arange(ny), np.arange(nz)
+    fx = np.cos(math.pi * a * (i + 0.5) / nx) if walls[0] else np.cos(2 * math.pi * a * i / nx)
+    fy = np.cos(math.pi * b * (j + 0.5) / ny) if walls[1] else np.cos(2 * math.pi * b * j / ny)
+    fz = np.cos(math.pi * c * (k + 0.5) / nz)
+    phi = fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+    lam = (_eig_lambda(a, nx, lx / nx, walls[0]) + _eig_lambda(b, ny, ly / ny, walls[1])
+           + _eig_lambda(c, 2 * nz, lz / nz, False))
+    p_n = synth.normal_np(9, 1, phi.shape)
+    dt, alpha, inv_re = 2e-3, 0.5, 1.0 / 40.0
+    got = O.pressure_update(g, p_n, phi, dt, alpha, inv_re)
+    assert rel(got, p_n + (1.0 - 0.5 * alpha * dt * inv_re * lam) * phi) < 1e-13
+    assert np.array_equal(O.pressure_update(g, p_n, phi, dt, alpha, 0.0), p_n + phi)
