@@ -225,7 +225,7 @@ SmemNeed smem_need(const ibf_grid &g, int mixed, const ibf_tuning &t) {
     const size_t csz = mixed ? 8 : 16, rsz = mixed ? 4 : 8;
     const int nx2 = g.nx / t.x_n1, ny2 = g.ny / t.y_n1;
     SmemNeed n{0, 0, 0, 0};
-    n.x = (size_t)(t.rows / 2) * (size_t)(t.x_n1 * (nx2 + 1)) * csz;
+    n.x = (size_t)(t.rows / 2) * (size_t)(t.x_n1 * (nx2 + 1) + 1) * csz;
     const size_t sstr = (size_t)(t.y_n1 * (ny2 + 1) + 1), nslot = (size_t)g.ny * t.mb;
     if (t.yz_kernel == 1) {  // layouts of k_yzfwd / k_yzbwd
         const size_t fwd = kYZStages * ((t.mb * sstr * csz + nslot * rsz + 15) & ~(size_t)15) + nslot * csz;

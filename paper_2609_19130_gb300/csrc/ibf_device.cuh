@@ -68,6 +68,12 @@ __device__ __forceinline__ df df_mulf(df a, float b) {
     return quick_two_sum(p, e);
 }
 __device__ __forceinline__ float df_to_f(df a) { return __fadd_rn(a.hi, a.lo); }
+// a + b + c of three floats as a normalised pair (error below 2^-47 of the largest term)
+__device__ __forceinline__ df sum3(float a, float b, float c) {
+    const df s = two_sum(a, b);
+    const df t = two_sum(s.hi, c);
+    return two_sum(t.hi, __fadd_rn(t.lo, s.lo));
+}
 
 // fp64 -> df32 without fp64 arithmetic.  hi takes the sign, the exponent and the
 // top 23 fraction bits (truncated); lo = x - hi is formed from the remaining 29

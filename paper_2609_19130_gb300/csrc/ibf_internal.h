@@ -93,7 +93,9 @@ struct UserPtrs {
     int blk0;                  // first block index (x-kernel numbering) of grid g0
 };
 
-enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2 };
+// x-forward modes: right-hand side of the first solve, refinement residual (phi a
+// float-float pair), adjoint source, refinement residual of the first sweep (phi plain fp32)
+enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2, XM_RESID0 = 3 };
 enum InvMode { IM_STORE = 0, IM_ACCUM = 1 };
 
 // Launchers (ibf_kernels.cu).  T = 0: fp64 path, 1: mixed path.

@@ -53,7 +53,10 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const int k = lb / nrb, rb = lb - k * nrb;
     const int j0 = rb * rows;
     const int nx = G.nx, ny = G.ny, nz = G.nz;
-    const int N1 = G.nx1, N2 = G.nx2, sstride = fft_seq_len(N1, N2);
+    // sequences one complex element further apart than their length, so that the
+    // split / gather steps, which read the same position of several sequences, do not
+    // fall into one shared-memory bank
+    const int N1 = G.nx1, N2 = G.nx2, sstride = fft_seq_len(N1, N2) + 1;
     const FDiv fN1 = G.fnx1, fN2 = G.fnx2;
     const int gi = g - p.g0;
     const int zo = G.z_off;
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
         const int ii = act ? i : nx - 1;  // inactive lanes load a valid cell and discard it
         // right neighbour: the next face of the u row (face nx when x is wall-bounded) on
         // the divergence paths, the next cell (periodic wrap) on the residual path
-        const int ip = (ii + 1 == nx && (MODE == XM_RESID || !wall_x)) ? 0 : ii + 1;
+        const int ip = (ii + 1 == nx && (MODE == XM_RESID || MODE == XM_RESID0 || !wall_x)) ? 0 : ii + 1;
         const int im = (ii == 0) ? nx - 1 : ii - 1;
         const bool own_up = (lane == 31) || (ii + 1 == nx);
         const bool own_dn = (lane == 0) || (ii == 0);
@@ -178,6 +181,79 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                     if (act) *(reinterpret_cast<T *>(buf + (jl >> 1) * sstride + spos) + (jl & 1)) = val;
                 }
             }
+        } else if constexpr (MODE == XM_RESID0 && IsDF<A>::value) {
+            // first refinement sweep: phi_0 is plain fp32, so the second differences are
+            // exact float sums (a missing wall neighbour is replaced by the cell itself,
+            // which zeroes its difference) and only the coefficient products and the
+            // final sums round, at float-float precision
+            const float *ph = w.phi_hi + G.cell_off + pbase;
+            const float2 *bd = w.bdf + G.cell_off + pbase;
+            float Pm = 0.f, Pc = 0.f;
+            bool have = false;
+            for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
+                float pn[kRowGroup], pkp[kRowGroup], pkm[kRowGroup], peu[kRowGroup], ped[kRowGroup];
+                float2 bdv[kRowGroup];
+                float pm0 = 0.f, pc0 = 0.f;
+                const bool need0 = !have;
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+                    pn[q] = pkp[q] = pkm[q] = peu[q] = ped[q] = 0.f;
+                    bdv[q] = make_float2(0.f, 0.f);
+                    if (jl < sm.r1 && j < ny) {
+                        const int jp = (j + 1 == ny) ? 0 : j + 1;
+                        const int jm = (j == 0) ? ny - 1 : j - 1;
+                        const int row = j * nx;
+                        if (q == 0 && need0) {
+                            pm0 = __ldg(ph + jm * nx + ii);
+                            pc0 = __ldg(ph + row + ii);
+                        }
+                        pn[q] = __ldg(ph + jp * nx + ii);
+                        if (k + 1 < nz) pkp[q] = __ldg(ph + plane + row + ii);
+                        if (k > 0) pkm[q] = __ldg(ph + row + ii - plane);
+                        if (own_up) peu[q] = __ldg(ph + row + ip);
+                        if (own_dn) ped[q] = __ldg(ph + row + im);
+                        if (act) bdv[q] = __ldg(bd + row + i);
+                    }
+                }
+                if (need0) {
+                    Pm = pm0;
+                    Pc = pc0;
+                }
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+                    if (jl >= sm.r1) break;
+                    T val = (T)0;
+                    if (j < ny) {
+                        float Pip = __shfl_down_sync(0xffffffffu, Pc, 1);
+                        if (own_up) Pip = peu[q];
+                        float Pim = __shfl_up_sync(0xffffffffu, Pc, 1);
+                        if (own_dn) Pim = ped[q];
+                        if (wall_x && ii + 1 == nx) Pip = Pc;
+                        if (wall_x && ii == 0) Pim = Pc;
+                        float Pjp = pn[q], Pjm = Pm;
+                        if (wall_y && j + 1 == ny) Pjp = Pc;
+                        if (wall_y && j == 0) Pjm = Pc;
+                        const float Pkp = (k + 1 < nz) ? pkp[q] : Pc, Pkm = (k > 0) ? pkm[q] : Pc;
+                        const df d2x = sum3(Pip, Pim, -2.f * Pc), d2y = sum3(Pjp, Pjm, -2.f * Pc);
+                        const df dzp = two_sum(Pkp, -Pc), dzm = two_sum(Pc, -Pkm);
+                        df lap = df_add(df_mul(cu, d2x), df_mul(cv, d2y));
+                        lap = df_add(lap, df_sub(df_mul(cwp, dzp), df_mul(cwm, dzm)));
+                        if (act) {
+                            const df bv = df_sub(df_sub(df{bdv[q].x, bdv[q].y}, cp), lap);
+                            acc_phi = df_addf(acc_phi, Pc);
+                            val = df_to_f(bv) * scale;
+                        }
+                        Pm = Pc;
+                        Pc = pn[q];
+                        have = true;
+                    } else {
+                        have = false;
+                    }
+                    if (act) *(reinterpret_cast<T *>(buf + (jl >> 1) * sstride + spos) + (jl & 1)) = val;
+                }
+            }
         } else {
             PhiSrc<A> ph;
             if constexpr (sizeof(T) == 4) {
@@ -240,7 +316,6 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                             V bvv = A::zero();
                             if constexpr (sizeof(T) == 4) bvv = df{bdv[q].x, bdv[q].y};
                             const V bv = A::sub(A::sub(bvv, cp), lap);
-                            acc = A::add(acc, bv);
                             acc_phi = A::add(acc_phi, Pc);
                             val = to_T<T, A>(bv) * scale;
                         }
@@ -255,10 +330,14 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
             }
         }
     }
-    // plane sums of this block's rows (for the singular mode), fixed reduction order
-    V tot = Red<A>::sum(acc, red);
-    if (threadIdx.x == 0) w.partial[G.part_off + k * nrb + rb] = A::store(tot);
-    if (MODE == XM_RESID) {
+    // plane sums of this block's rows (for the singular mode), fixed reduction order:
+    // of the right-hand side in the first pass; of phi in a refinement pass (k_00 forms
+    // the plane means of the residual from both, since x and y differences sum to zero
+    // over a plane)
+    if (MODE == XM_DIV || MODE == XM_ADJ) {
+        V tot = Red<A>::sum(acc, red);
+        if (threadIdx.x == 0) w.partial[G.part_off + k * nrb + rb] = A::store(tot);
+    } else {
         V totp = Red<A>::sum(acc_phi, red);
         if (threadIdx.x == 0) w.partial_phi[G.part_off + k * nrb + rb] = A::store(totp);
     }
@@ -314,7 +393,10 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const int k = lb / nrb, rb = lb - k * nrb;
     const int j0 = rb * rows;
     const int nx = G.nx, ny = G.ny;
-    const int N1 = G.nx1, N2 = G.nx2, sstride = fft_seq_len(N1, N2);
+    // sequences one complex element further apart than their length, so that the
+    // split / gather steps, which read the same position of several sequences, do not
+    // fall into one shared-memory bank
+    const int N1 = G.nx1, N2 = G.nx2, sstride = fft_seq_len(N1, N2) + 1;
     const FDiv fN1 = G.fnx1, fN2 = G.fnx2, fmb = G.fmb, fnpair = G.fnpair, fnx = G.fnx;
     const int mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const cx<T> *spec = reinterpret_cast<const cx<T> *>(w.spec) + G.spec_off + (size_t)k * ncb * ny * mb;
@@ -429,7 +511,7 @@ __global__ void __launch_bounds__(kXThreads, 4)
     // or p_n + phi [- cimp (b - <b>)] (Eq. pressure) with p_n = in.p
     double *po = (!ADJ && (MIX || PU)) ? p.out_p[gi] + pbase : nullptr;
     const double *pn = (!ADJ && PU) ? p.in_p[gi] + pbase : nullptr;
-    const double mean_b = w.mean_b[g];
+    const double mean_b = PU ? w.mean_b[g] : 0.0;
     V cu, cv, cw;
     if (ADJ) {
         const double hz = w.z.hz[zo + k];
@@ -600,6 +682,8 @@ cudaError_t launch_xfwd_w(int mixed, int mode, const Work &w, const UserPtrs &p,
     if (mixed) {
         if (mode == XM_DIV)
             k_xfwd<float, DFArith, XM_DIV, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        else if (mode == XM_RESID && !lo_valid)
+            k_xfwd<float, DFArith, XM_RESID0, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else if (mode == XM_RESID)
             k_xfwd<float, DFArith, XM_RESID, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else
@@ -708,6 +792,7 @@ cudaError_t set_smem_limits(int mixed) {
         if (mixed) {
             set((const void *)k_xfwd<float, DFArith, XM_DIV, W>);
             set((const void *)k_xfwd<float, DFArith, XM_RESID, W>);
+            set((const void *)k_xfwd<float, DFArith, XM_RESID0, W>);
             set((const void *)k_xfwd<float, DFArith, XM_ADJ, W>);
             set((const void *)k_xinv<float, DFArith, IM_STORE, W>);
             set((const void *)k_xinv<float, DFArith, IM_ACCUM, W>);

@@ -159,7 +159,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     d.fmb = fdiv_of(d.mb); d.frows = fdiv_of(d.rows); d.fnpair = fdiv_of(d.rows / 2);
     const size_t cells = (size_t)d.nx * d.ny * nz;
     const size_t nspec = (size_t)nz * d.ncb * d.ny * d.mb;
-    const size_t xsmem = (size_t)(d.rows / 2) * (size_t)(d.nx1 * (d.nx2 + 1)) * csz;
+    const size_t xsmem = (size_t)(d.rows / 2) * (size_t)(d.nx1 * (d.nx2 + 1) + 1) * csz;
     size_t yzsmem;
     {
         const size_t sstr = (size_t)(d.ny1 * (d.ny2 + 1) + 1), nslot = (size_t)d.ny * d.mb;

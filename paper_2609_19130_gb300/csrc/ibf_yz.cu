@@ -516,25 +516,40 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     double *A0 = sh00 + 2 * L, *B0 = A0 + L, *C0 = B0 + L, *D0 = C0 + L;
     double *A1 = D0 + L, *B1 = A1 + L, *C1 = B1 + L, *D1 = C1 + L;
     const double *part = w.partial + G.part_off;
+    double *Pk = A1;  // plane means of the phi being refined (A1 is free until the PCR steps)
     double loc = 0.0, locp = 0.0;
     bool bad = false;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         double S = 0.0;
         for (int r = 0; r < nrb; ++r) S += part[k * nrb + r];
-        const double m = S * G.inv_nxy;  // plane mean of the right-hand side
+        const double m = S * G.inv_nxy;  // plane mean of the first right-hand side b
         if (!isfinite(m)) bad = true;
         const double h = w.z.hz[zo + k];
         rhs[k] = m;
         hz[k] = h;
-        loc += h * m;
         if (!first_solve) {
             double P = 0.0;
             for (int r = 0; r < nrb; ++r) P += w.partial_phi[G.part_off + k * nrb + r];
-            locp += h * P * G.inv_nxy;
+            Pk[k] = P * G.inv_nxy;
+            locp += h * Pk[k];
         }
     }
     if (bad) atomicOr(w.err, 1u << 6);  // IBF_ERR_NONFINITE
     __syncthreads();
+    if (!first_solve) {
+        // plane mean of the refinement residual b - <b> - L phi: the x and y differences of
+        // L phi sum to zero over a plane (periodic wrap or Neumann walls), so it is the
+        // plane mean of b, less <b>, less the z part of L applied to the plane means of phi
+        const double mb = w.mean_b[g];
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+            double lz = 0.0;
+            if (k + 1 < nz) lz += w.z.cz[zo + k] * (Pk[k + 1] - Pk[k]);
+            if (k > 0) lz -= w.z.az[zo + k] * (Pk[k] - Pk[k - 1]);
+            rhs[k] = rhs[k] - mb - lz;
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) loc += hz[k] * rhs[k];
     const double tot = Red<F64Arith>::sum(loc, red);
     // weighted mean of the phi being refined: the correction also removes it, so that
     // phi + delta keeps a zero weighted mean (L cannot see a constant)
