@@ -17,10 +17,12 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def operators(nx, ny, nz, lx, ly, zf, wall_x=False, wall_y=False):
+def operators(nx, ny, nz, lx, ly, zf, wall_x=False, wall_y=False, dirichlet_top=False):
     """Return (D, G, Vc) with D: faces -> cells, G: cells -> faces (sparse CSR).
 
-    Face ordering: all u faces, then v faces, then w faces, each [k][j][i]."""
+    Face ordering: all u faces, then v faces, then w faces, each [k][j][i].  With a
+    Dirichlet outlet, phi = 0 on the top face: G there is the one-sided difference to
+    that face, (0 - phi_{nz-1}) / (zf_nz - zc_{nz-1})."""
     zf = np.asarray(zf, dtype=np.float64)
     dx, dy = lx / nx, ly / ny
     hz = zf[1:] - zf[:-1]
@@ -77,6 +79,13 @@ def operators(nx, ny, nz, lx, ly, zf, wall_x=False, wall_y=False):
                 grows += [wid(k, j, i)] * 2
                 gcols += [cid(k, j, i), cid(k - 1, j, i)]
                 gvals += [1 / gz, -1 / gz]
+    if dirichlet_top:
+        gtop = zf[nz] - zc[nz - 1]
+        for j in range(ny):
+            for i in range(nx):
+                grows += [wid(nz, j, i)]
+                gcols += [cid(nz - 1, j, i)]
+                gvals += [-1 / gtop]
     D = sp.csr_matrix((vals, (rows, cols)), shape=(ncells, nf))
     G = sp.csr_matrix((gvals, (grows, gcols)), shape=(nf, ncells))
     Vc = np.repeat(dx * dy * hz, nx * ny)
@@ -86,16 +95,19 @@ def operators(nx, ny, nz, lx, ly, zf, wall_x=False, wall_y=False):
 class DenseProjection:
     """P(u*) and its exact transpose with dense linear algebra."""
 
-    def __init__(self, nx, ny, nz, lx, ly, zf, wall_x=False, wall_y=False):
+    def __init__(self, nx, ny, nz, lx, ly, zf, wall_x=False, wall_y=False, dirichlet_top=False):
         self.shape = (nx, ny, nz)
         self.wall_x, self.wall_y = wall_x, wall_y
-        self.D, self.G, self.Vc = operators(nx, ny, nz, lx, ly, zf, wall_x, wall_y)
+        self.D, self.G, self.Vc = operators(nx, ny, nz, lx, ly, zf, wall_x, wall_y, dirichlet_top)
         n = nx * ny * nz
         L = (self.D @ self.G).toarray()
-        A = np.zeros((n + 1, n + 1))
-        A[:n, :n] = L
-        A[:n, n] = 1.0
-        A[n, :n] = self.Vc
+        if dirichlet_top:                 # nonsingular: no bordering
+            A = L
+        else:
+            A = np.zeros((n + 1, n + 1))
+            A[:n, :n] = L
+            A[:n, n] = 1.0
+            A[n, :n] = self.Vc
         self.A = A
         self.Ainv = np.linalg.inv(A)      # small problems only
         self.n = n
@@ -116,7 +128,7 @@ class DenseProjection:
         return a, b, c
 
     def solve(self, b):
-        rhs = np.concatenate([np.ravel(b), [0.0]])
+        rhs = np.ravel(b) if self.A.shape[0] == self.n else np.concatenate([np.ravel(b), [0.0]])
         x = np.linalg.solve(self.A, rhs)
         return x[:self.n]
 

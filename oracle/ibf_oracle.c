@@ -38,6 +38,13 @@
  *  R4 wall-bounded x (or y), not used by the paper: u has nx+1 faces,
  *     u[..][..][0] and u[..][..][nx] are walls, and the x transform is DCT-II.
  *  R5 tanh stretching: zf_k = lz/2 (1 + tanh(beta (2k/nz - 1)) / tanh(beta)).
+ *  R6 Dirichlet outlet (boundary-condition paragraph of the same section: with
+ *     neumann_velocity the pressure-correction equation takes a homogeneous
+ *     Dirichlet condition at the outlet): phi = 0 on the top face z = lz, taken
+ *     through the mirror value -phi_{nz-1}, so G phi on the top face is
+ *     -phi_{nz-1} / (lz - zc_{nz-1}) and the top face velocity is corrected.  L is
+ *     then nonsingular: no compatibility mean is removed and no reference value is
+ *     fixed.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (see build_oracle.py).
  */
@@ -52,6 +59,7 @@ typedef struct {
     double lx, ly;
     const double *zf;   /* nz+1 ascending face coordinates */
     int wall_x, wall_y; /* 0: periodic, 1: walls (Neumann phi, DCT) */
+    int dirichlet_top;  /* 0: Neumann phi at z = lz; 1: phi = 0 there (R6) */
 } ibfo_grid;
 
 /* ------------------------------------------------------------------ grid */
@@ -74,6 +82,8 @@ static int nyv_of(const ibfo_grid *g) { return g->wall_y ? g->ny + 1 : g->ny; }
 static double hz_of(const ibfo_grid *g, int k) { return g->zf[k + 1] - g->zf[k]; }
 static double zc_of(const ibfo_grid *g, int k) { return 0.5 * (g->zf[k] + g->zf[k + 1]); }
 static double gz_of(const ibfo_grid *g, int k) { return zc_of(g, k) - zc_of(g, k - 1); } /* 1<=k<=nz-1 */
+/* distance from the last cell centre to the top face (R6) */
+static double gtop_of(const ibfo_grid *g) { return g->zf[g->nz] - zc_of(g, g->nz - 1); }
 
 /* ------------------------------------------------------- R2: D, G, L */
 
@@ -132,6 +142,8 @@ void ibfo_gradient(const ibfo_grid *g, const double *phi, double *gu, double *gv
                 double val = 0.0;
                 if (k > 0 && k < nz)
                     val = (phi[((size_t)k * ny + j) * nx + i] - phi[((size_t)(k - 1) * ny + j) * nx + i]) / gz_of(g, k);
+                else if (k == nz && g->dirichlet_top)
+                    val = (0.0 - phi[((size_t)(k - 1) * ny + j) * nx + i]) / gtop_of(g);
                 gw[((size_t)k * ny + j) * nx + i] = val;
             }
     }
@@ -188,6 +200,12 @@ void ibfo_gradient_T(const ibfo_grid *g, const double *gu, const double *gv, con
                 out[((size_t)k * ny + j) * nx + i] += f;
                 out[((size_t)(k - 1) * ny + j) * nx + i] -= f;
             }
+    }
+    if (g->dirichlet_top) {
+        double rg = 1.0 / gtop_of(g);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                out[((size_t)(nz - 1) * ny + j) * nx + i] -= gw[((size_t)nz * ny + j) * nx + i] * rg;
     }
 }
 
@@ -327,7 +345,9 @@ static void thomas(const double *a, const double *d, const double *c, const doub
 /* ------------------------------------------------------- Poisson solve */
 
 /* phi = S^-1 b : the unique phi with L phi = b - <b>_V and <phi>_V = 0
- * (reading R3).  Returns <b>_V in *compat.  b is not modified. */
+ * (reading R3), or with a Dirichlet outlet (R6) the unique phi with L phi = b.
+ * Returns the removed <b>_V (0 with a Dirichlet outlet) in *compat.  b is not
+ * modified. */
 int ibfo_poisson(const ibfo_grid *g, const double *b, double *phi, double *compat)
 {
     const int nx = g->nx, ny = g->ny, nz = g->nz;
@@ -342,12 +362,13 @@ int ibfo_poisson(const ibfo_grid *g, const double *b, double *phi, double *compa
         az[k] = (k > 0) ? 1.0 / (hz * gz_of(g, k)) : 0.0;
         cz[k] = (k < nz - 1) ? 1.0 / (hz * gz_of(g, k + 1)) : 0.0;
         bz[k] = -(az[k] + cz[k]);
+        if (k == nz - 1 && g->dirichlet_top) bz[k] -= 1.0 / (hz * gtop_of(g));  /* flux to phi = 0 */
         double s = 0.0;
         for (size_t p = 0; p < plane; ++p) s += b[(size_t)k * plane + p];
         sumVb += hz * s;          /* dx dy cancels in the weighted mean */
         sumV += hz * (double)plane;
     }
-    const double mean_b = sumVb / sumV;
+    const double mean_b = g->dirichlet_top ? 0.0 : sumVb / sumV;
     if (compat) *compat = mean_b;
 
     /* spectral coefficients: spec[k][n][m] */
@@ -387,7 +408,7 @@ int ibfo_poisson(const ibfo_grid *g, const double *b, double *phi, double *compa
         for (long long mode = 0; mode < (long long)plane; ++mode) {
             int n = (int)(mode / nx), m = (int)(mode % nx);
             double lam = lambda_1d(m, nx, dx, g->wall_x) + lambda_1d(n, ny, dy, g->wall_y);
-            int k0 = (m == 0 && n == 0) ? 1 : 0;   /* pin the first level of the singular mode */
+            int k0 = (m == 0 && n == 0 && !g->dirichlet_top) ? 1 : 0;   /* pin the first level of the singular mode */
             for (int k = 0; k < nz; ++k) d[k] = bz[k] + lam;
             for (int part = 0; part < 2; ++part) {
                 for (int k = 0; k < nz; ++k) {
@@ -433,7 +454,7 @@ int ibfo_poisson(const ibfo_grid *g, const double *b, double *phi, double *compa
         for (size_t p = 0; p < plane; ++p) s += phi[(size_t)k * plane + p];
         sVp += hz_of(g, k) * s;
     }
-    const double mean_phi = sVp / sumV;
+    const double mean_phi = g->dirichlet_top ? 0.0 : sVp / sumV;
     for (size_t c = 0; c < plane * nz; ++c) phi[c] -= mean_phi;
 
     xform_free(&tx); xform_free(&ty);

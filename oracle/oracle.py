@@ -38,7 +38,8 @@ def lib():
 class _CGrid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("lx", C.c_double), ("ly", C.c_double),
-                ("zf", C.POINTER(C.c_double)), ("wall_x", C.c_int), ("wall_y", C.c_int)]
+                ("zf", C.POINTER(C.c_double)), ("wall_x", C.c_int), ("wall_y", C.c_int),
+                ("dirichlet_top", C.c_int)]
 
 
 def _p(a):
@@ -63,13 +64,14 @@ class Grid:
     zf: np.ndarray | None = None
     wall_x: bool = False
     wall_y: bool = False
+    dirichlet_top: bool = False
 
     def __post_init__(self):
         if self.zf is None:
             self.zf = zfaces_tanh(self.nz, self.lz, self.beta)
         self.zf = np.ascontiguousarray(self.zf, dtype=np.float64)
         self._c = _CGrid(self.nx, self.ny, self.nz, self.lx, self.ly, _p(self.zf),
-                         int(self.wall_x), int(self.wall_y))
+                         int(self.wall_x), int(self.wall_y), int(self.dirichlet_top))
 
     @property
     def cptr(self):

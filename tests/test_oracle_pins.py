@@ -300,3 +300,63 @@ def test_pressure_update_closed_form(walls):
     got = O.pressure_update(g, p_n, phi, dt, alpha, inv_re)
     assert rel(got, p_n + (1.0 - 0.5 * alpha * dt * inv_re * lam) * phi) < 1e-13
     assert np.array_equal(O.pressure_update(g, p_n, phi, dt, alpha, 0.0), p_n + phi)
+
+
+# ---------------------------------------------------------------- Dirichlet outlet (phi = 0 at z = lz)
+@pytest.mark.parametrize("shape,beta,walls", [
+    ((8, 8, 8), 2.0, (False, False)), ((6, 12, 5), 0.0, (False, False)), ((6, 4, 7), 1.5, (True, True)),
+    ((1, 1, 9), 2.5, (False, False)),
+])
+def test_dirichlet_outlet_matches_dense_solve(shape, beta, walls):
+    """No compatibility mean, no reference value: phi solves L phi = D u*/(alpha dt)
+    exactly (dense LU of the nonsingular L), and the top face velocity is corrected."""
+    nx, ny, nz = shape
+    g = O.Grid(nx, ny, nz, lx=1.3, ly=0.7, lz=2.0, beta=beta, wall_x=walls[0], wall_y=walls[1],
+               dirichlet_top=True)
+    u, v, w = synth.uniform_velocity_np(8, nx, ny, nz, *walls, zero_walls=False)
+    phi, uu, vv, ww, st = O.project(g, u, v, w, dt=1e-3, alpha=1.0)
+    dp = dense.DenseProjection(nx, ny, nz, 1.3, 0.7, g.zf, *walls, dirichlet_top=True)
+    phid, ud, vd, wd = dp.project(u, v, w, dt=1e-3, alpha=1.0)
+    assert rel(phi, phid) < TOL
+    for a, b in ((uu, ud), (vv, vd), (ww, wd)):
+        assert np.max(np.abs(a - b)) < TOL * max(1.0, np.max(np.abs(b)))
+    assert st[2] == 0.0                                     # nothing removed
+    assert st[0] <= 1e-10 * st[1]                           # divergence-free, incl. the top cells
+    assert np.array_equal(ww[0], w[0])                      # the bottom wall is untouched
+    assert not np.allclose(ww[-1], w[-1])                   # the outlet face is corrected
+
+
+@pytest.mark.parametrize("a,b,c", [(0, 0, 0), (1, 2, 0), (0, 0, 3), (2, 1, 4)])
+def test_dirichlet_outlet_eigenfunctions(a, b, c):
+    """Uniform z, Neumann bottom and Dirichlet top: cos(pi (c+1/2)(k+1/2)/nz) is a discrete
+    eigenfunction of the z second difference with eigenvalue -4/h^2 sin^2(pi (2c+1)/(4 nz))
+    (the continued cosine vanishes on the top face, so its mirror value is -phi_{nz-1}).
+    The (0,0,0) mode is regular here: the solver must return it, without mean removal."""
+    nx, ny, nz = 12, 8, 10
+    lx, ly, lz = 1.1, 0.9, 1.6
+    g = O.Grid(nx, ny, nz, lx=lx, ly=ly, lz=lz, beta=0.0, dirichlet_top=True)
+    i, j, k = np.arange(nx), np.arange(ny), np.arange(nz)
+    fx = np.cos(2 * math.pi * a * i / nx)
+    fy = np.cos(2 * math.pi * b * j / ny)
+    fz = np.cos(math.pi * (c + 0.5) * (k + 0.5) / nz)
+    phi_e = fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+    hz = lz / nz
+    lam = (_eig_lambda(a, nx, lx / nx, False) + _eig_lambda(b, ny, ly / ny, False)
+           - 4.0 / hz ** 2 * math.sin(math.pi * (2 * c + 1) / (4 * nz)) ** 2)
+    assert rel(O.laplacian(g, phi_e), lam * phi_e) < 1e-12
+    phi, compat = O.poisson(g, lam * phi_e)
+    assert compat == 0.0
+    assert rel(phi, phi_e) < TOL
+
+
+def test_dirichlet_outlet_adjoint_matches_dense_transpose():
+    nx, ny, nz = 6, 4, 6
+    g = O.Grid(nx, ny, nz, lx=1.1, ly=0.9, lz=2.0, beta=2.0, dirichlet_top=True)
+    su, sv, sw = g.shapes
+    gu, gv, gw = (synth.normal_np(17, t, s) for t, s in ((1, su), (2, sv), (3, sw)))
+    gp = synth.normal_np(17, 4, g.cshape)
+    a, b, c = O.project_adjoint(g, gu, gv, gw, gp, dt=2e-3, alpha=0.5)
+    dp = dense.DenseProjection(nx, ny, nz, 1.1, 0.9, g.zf, dirichlet_top=True)
+    ad, bd, cd = dp.project_T(gu, gv, gw, gp, dt=2e-3, alpha=0.5)
+    for x, y in ((a, ad), (b, bd), (c, cd)):
+        assert rel(x, y) < 1e-11
