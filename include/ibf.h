@@ -35,7 +35,8 @@
  *   (D u)_c = (u_{i+1}-u_i)/dx + (v_{j+1}-v_j)/dy + (w_{k+1}-w_k)/hz_k (wrap in a
  *   periodic direction);
  *   G phi on interior faces (difference over dx, dy or gz_k), zero on the walls,
- *   so the wall-normal velocity is left unchanged.
+ *   so the wall-normal velocity is left unchanged (a Dirichlet outlet instead takes
+ *   -phi_{nz-1} / (lz - zc_{nz-1}) on the top face).
  *   Reference value: the volume-weighted mean of the right-hand side is removed
  *   (its value is reported as the compatibility defect) and phi is returned
  *   with zero volume-weighted mean (weights dx dy hz_k).
@@ -63,14 +64,15 @@ typedef enum ibf_status {
     IBF_ERR_TIMEOUT = 5,          /* a bounded device wait gave up (reported by ibf_plan_sync_status) */
     IBF_ERR_NONFINITE = 6,        /* NaN or Inf met in the right-hand side (ibf_plan_sync_status) */
     IBF_WARN_INCOMPATIBLE_RHS = 7,/* |compatibility defect| above 1e-8 of the RHS scale; result still returned */
-    IBF_ERR_UNSUPPORTED_BC = 8    /* a boundary condition this build does not implement
-                                     (Dirichlet; walls in x or y for ibf_project_noalloc) */
+    IBF_ERR_UNSUPPORTED_BC = 8    /* a boundary condition this build does not implement (Dirichlet in
+                                     x, y or at the bottom, periodic z; for ibf_project_noalloc also
+                                     walls in x or y and a Dirichlet outlet) */
 } ibf_status;
 
 typedef enum ibf_bc {
     IBF_BC_PERIODIC = 0,
     IBF_BC_NEUMANN = 1,           /* wall: prescribed normal velocity, homogeneous Neumann phi */
-    IBF_BC_DIRICHLET = 2          /* homogeneous Dirichlet phi (not implemented: UNSUPPORTED_BC) */
+    IBF_BC_DIRICHLET = 2          /* homogeneous Dirichlet phi: the top (outlet) face only */
 } ibf_bc;
 
 /* Output pressure (paper Eq. pressure).  IBF_P_PHI: out.p = phi.  IBF_P_EXPLICIT:
@@ -100,7 +102,10 @@ typedef struct ibf_grid {
     double beta;            /* tanh clustering factor when zf == NULL:
                                zf_k = lz/2 (1 + tanh(beta (2k/nz - 1)) / tanh(beta)); beta = 0: uniform */
     int bc_x, bc_y;         /* ibf_bc: IBF_BC_PERIODIC, or IBF_BC_NEUMANN (walls, DCT-II) */
-    int bc_zlo, bc_zhi;     /* ibf_bc; this build: IBF_BC_NEUMANN */
+    int bc_zlo, bc_zhi;     /* ibf_bc: bc_zlo IBF_BC_NEUMANN; bc_zhi IBF_BC_NEUMANN, or IBF_BC_DIRICHLET
+                               for an outlet (phi = 0 on the top face through the mirror value
+                               -phi_{nz-1}; the top face velocity is then corrected, and no
+                               compatibility mean or reference value is involved) */
 } ibf_grid;
 
 typedef struct ibf_opts {
@@ -115,14 +120,17 @@ typedef struct ibf_opts {
     double inv_re;          /* 1/Re of the implicit viscous term (IBF_P_IMPLICIT; >= 0) */
 } ibf_opts;
 
-/* DEVICE pointers (float64, layouts above) of one grid. */
+/* DEVICE pointers (float64, layouts above) of one grid.  q (input only, may be NULL =
+ * zero): the cell-centred mass source of Eq. (elliptic), lap(phi) = (D u* - q)/(alpha dt),
+ * layout of p; with it the projected velocity satisfies D u = q. */
 typedef struct ibf_fields {
     double *u, *v, *w, *p;
+    const double *q;
 } ibf_fields;
 
 /* Optional DEVICE outputs, each an array of ngrids doubles (any pointer may be NULL).
- * max_div     : max_c |(D u_{n+1})_c| of the returned velocity;
- * max_div_in  : max_c |(D u*)_c|;
+ * max_div     : max_c |(D u_{n+1} - q)_c| of the returned velocity (q = 0 if absent);
+ * max_div_in  : max_c |(D u* - q)_c|;
  * compat      : removed volume-weighted mean of div(u*)/(alpha dt). */
 typedef struct ibf_stats {
     double *max_div, *max_div_in, *compat;

@@ -148,6 +148,16 @@ def project(g: Grid, us, vs, ws, dt=1e-3, alpha=1.0):
     return phi, u, v, w, st
 
 
+def project_q(g: Grid, us, vs, ws, q, dt=1e-3, alpha=1.0):
+    """Eq. (elliptic) with a mass source: lap(phi) = (D u* - q)/(alpha dt), then Eq. (velsolen)
+    u = u* - alpha dt G phi.  Returns (phi, u, v, w, removed weighted mean of the rhs)."""
+    b = (divergence(g, us, vs, ws) - np.asarray(q, dtype=np.float64)) / (alpha * dt)
+    phi, compat = poisson(g, b)
+    gu, gv, gw = gradient(g, phi)
+    s = alpha * dt
+    return phi, us - s * gu, vs - s * gv, ws - s * gw, compat
+
+
 def pressure_update(g: Grid, p_n, phi, dt=1e-3, alpha=1.0, inv_re=0.0):
     """Eq. (pressure) (Section "Fluid Mechanics"): p_{n+1} = p_n + phi - alpha dt/(2 Re) lap(phi),
     with the discrete Laplacian L = D G of the projection; inv_re = 0 is the explicit-viscous

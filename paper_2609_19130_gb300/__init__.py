@@ -126,17 +126,21 @@ class Plan:
         return self._h
 
     def project_into(self, ins, outs, dt, alpha=1.0, stats=None, stream=None):
-        """ins/outs: per grid (u, v, w[, p]) CUDA float64 tensors; outs need p."""
+        """ins: per grid (u, v, w[, p_n[, q]]) CUDA float64 tensors (p_n for a pressure-update
+        plan, q a cell-centred mass source of Eq. elliptic; either may be None); outs:
+        per grid (u, v, w, p)."""
         n = len(self.grids)
         fin = (N.ibf_fields * n)()
         fout = (N.ibf_fields * n)()
         for g in range(n):
             u, v, w = ins[g][:3]
             pn = ins[g][3] if len(ins[g]) > 3 else None
+            qs = ins[g][4] if len(ins[g]) > 4 else None
             if self.pressure != N.IBF_P_PHI and pn is None:
                 raise ValueError("this plan updates the pressure: pass (u, v, w, p_n) per grid")
             uo, vo, wo, po = outs[g]
-            fin[g] = N.ibf_fields(u.data_ptr(), v.data_ptr(), w.data_ptr(), pn.data_ptr() if pn is not None else None)
+            fin[g] = N.ibf_fields(u.data_ptr(), v.data_ptr(), w.data_ptr(), pn.data_ptr() if pn is not None else None,
+                                  qs.data_ptr() if qs is not None else None)
             fout[g] = N.ibf_fields(uo.data_ptr(), vo.data_ptr(), wo.data_ptr(), po.data_ptr())
         st_ptr = None
         if stats is not None:
@@ -158,13 +162,13 @@ class Plan:
         N.check(s, "ibf_project_backward")
 
     # ------------------------------------------------------------ conveniences
-    def project(self, u, v, w, dt, alpha=1.0, out=None, stats=False, stream=None, p=None):
+    def project(self, u, v, w, dt, alpha=1.0, out=None, stats=False, stream=None, p=None, q=None):
         """Single-grid convenience: returns (u, v, w, p) (new tensors unless `out` is given);
-        `p` is p_n for plans with a pressure update."""
+        `p` is p_n for plans with a pressure update, `q` an optional mass source."""
         import torch
         if len(self.grids) != 1:
             raise ValueError("project() is for single-grid plans; use project_batch()")
-        res = self.project_batch([(u, v, w) if p is None else (u, v, w, p)], dt, alpha,
+        res = self.project_batch([(u, v, w, p, q)], dt, alpha,
                                  out=[out] if out is not None else None, stats=stats, stream=stream)
         return res[0] if not stats else (res[0][0], res[1])
 
@@ -177,8 +181,9 @@ class Plan:
             su, sv, sw = grid.shapes
             for t, sh, nm in zip(f[:3], (su, sv, sw), ("u", "v", "w")):
                 _check_field(t, sh, nm)
-            if len(f) > 3 and f[3] is not None:
-                _check_field(f[3], (grid.nz, grid.ny, grid.nx), "p")
+            for extra, nm in zip(f[3:5], ("p", "q")):
+                if extra is not None:
+                    _check_field(extra, (grid.nz, grid.ny, grid.nx), nm)
             if out is not None:
                 o = out[g]
             else:

@@ -46,7 +46,7 @@ class ibf_opts(C.Structure):
 
 
 class ibf_fields(C.Structure):
-    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p), ("p", C.c_void_p)]
+    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p), ("p", C.c_void_p), ("q", C.c_void_p)]
 
 
 class ibf_stats(C.Structure):

@@ -140,7 +140,7 @@ ibf_status validate(const ibf_grid *g, std::vector<double> &zf) {
     for (int b : bcs)
         if (b < IBF_BC_PERIODIC || b > IBF_BC_DIRICHLET) return IBF_ERR_INVALID_ARG;
     if (g->bc_x == IBF_BC_DIRICHLET || g->bc_y == IBF_BC_DIRICHLET) return IBF_ERR_UNSUPPORTED_BC;
-    if (g->bc_zlo != IBF_BC_NEUMANN || g->bc_zhi != IBF_BC_NEUMANN) return IBF_ERR_UNSUPPORTED_BC;
+    if (g->bc_zlo != IBF_BC_NEUMANN || g->bc_zhi == IBF_BC_PERIODIC) return IBF_ERR_UNSUPPORTED_BC;
     int a, b;
     if (!factor(g->nx, &a, &b) || !factor(g->ny, &a, &b)) return IBF_ERR_UNSUPPORTED_SIZE;
     const int nz = g->nz;
@@ -304,6 +304,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         memset(&d, 0, sizeof(d));
         d.nx = H.g.nx; d.ny = H.g.ny; d.nz = H.g.nz;
         d.nxh = x_modes(H.g);
+        d.dir_top = H.g.bc_zhi == IBF_BC_DIRICHLET;
         d.wall_x = H.g.bc_x == IBF_BC_NEUMANN;
         d.wall_y = H.g.bc_y == IBF_BC_NEUMANN;
         d.nxu = d.nx + d.wall_x;
@@ -417,6 +418,12 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         for (int k = 0; k < nz; ++k) {
             az[o + k] = rhz[o + k] * rgzf[o + k];
             cz[o + k] = rhz[o + k] * rgzf[o + k + 1];
+        }
+        if (H.d.dir_top) {
+            // outlet face: phi = 0 there, so the flux through it couples level nz-1 to
+            // the face value only (an extra diagonal term, no coupling coefficient)
+            rgzf[o + nz] = 1.0 / (zf[nz] - 0.5 * (zf[nz - 1] + zf[nz]));
+            pl->grids[g].d.ez_top = rhz[o + nz - 1] * rgzf[o + nz];
         }
         // pinned (0,0) system: level 0 fixed to zero
         double cp = 0.0;
@@ -582,7 +589,10 @@ void fill_ptrs(ibf_plan *pl, UserPtrs &p, int g0, int g1, const ibf_fields *in, 
     p.blk0 = pl->grids[g0].d.xblk_off;
     for (int g = g0; g < g1; ++g) {
         const int i = g - g0;
-        if (in) { p.in_u[i] = in[g].u; p.in_v[i] = in[g].v; p.in_w[i] = in[g].w; p.in_p[i] = in[g].p; }
+        if (in) {
+            p.in_u[i] = in[g].u; p.in_v[i] = in[g].v; p.in_w[i] = in[g].w; p.in_p[i] = in[g].p;
+            p.in_q[i] = in[g].q;
+        }
         if (out) { p.out_u[i] = out[g].u; p.out_v[i] = out[g].v; p.out_w[i] = out[g].w; p.out_p[i] = out[g].p; }
     }
 }
@@ -644,7 +654,9 @@ ibf_status run(ibf_plan *pl, const ibf_fields *in, const ibf_fields *out, double
     cudaError_t e = cudaMemsetAsync(w.maxb, 0, sizeof(unsigned long long) * pl->ngrids, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.maxdiv, 0, sizeof(unsigned long long) * pl->ngrids, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    const int xmode = adjoint ? XM_ADJ : XM_DIV;
+    bool has_q = false;  // mass sources enter the forward map only (the adjoint is of u* -> (u, phi))
+    for (int g = 0; g < pl->ngrids && !adjoint; ++g) has_q |= in[g].q != nullptr;
+    const int xmode = adjoint ? XM_ADJ : (has_q ? XM_DIVQ : XM_DIV);
     IBF_TRY(for_chunks(c, adjoint ? "x_forward_adjoint_rhs" : "x_forward_div", in, out, [&](const UserPtrs &p, int nb) {
         return launch_xfwd(mixed, xmode, w, p, use_ws, 0, nb, s, rs, pl->xsmem, st);
     }));
@@ -716,8 +728,8 @@ ibf_status make_plan(ibf_plan **plan, const ibf_grid *grids, int ngrids, const i
 // algorithm that fits shared memory).  Results are cached per (shape, boundary
 // conditions, precision, refinement, forced fields) for the life of the process.
 struct TuneKey {
-    int v[13];
-    bool operator<(const TuneKey &o) const { return std::lexicographical_compare(v, v + 13, o.v, o.v + 13); }
+    int v[14];
+    bool operator<(const TuneKey &o) const { return std::lexicographical_compare(v, v + 14, o.v, o.v + 14); }
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, ibf_tuning> g_tune_cache;
@@ -758,9 +770,9 @@ float time_shape(TuneBench &b, const ibf_tuning &t) {
 
 ibf_status tune_grid(const ibf_grid &g, const ibf_opts &opts, int device, ibf_tuning *t) {
     TuneKey key;
-    const int kv[13] = {g.nx, g.ny, g.nz, g.bc_x, g.bc_y, opts.precision, opts.refine_steps,
+    const int kv[14] = {g.nx, g.ny, g.nz, g.bc_x, g.bc_y, g.bc_zhi, opts.precision, opts.refine_steps,
                         t->rows, t->x_n1, t->y_n1, t->yz_kernel, t->mb, t->tri};
-    std::copy(kv, kv + 13, key.v);
+    std::copy(kv, kv + 14, key.v);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);

@@ -27,6 +27,8 @@ struct GridDev {
     int wall_x, wall_y;        // 1: that direction is wall-bounded (Neumann phi, DCT-II transform)
     int nxu, nyv;              // faces of u per row (nx + wall_x), rows of v per plane (ny + wall_y)
     int dctx_off, dcty_off;    // offsets of the exp(-i pi m/(2N)) tables of the DCTs (in twx / twy)
+    int dir_top;               // 1: homogeneous Dirichlet phi on the top face (outlet), else Neumann
+    double ez_top;             // Dirichlet outlet: extra diagonal of level nz-1, rhz / (lz - zc_{nz-1})
     int yzk;                   // y/z kernels: 0 streaming (k_yzfwd + k_yzbwd), 1 resident slab (k_yzslab),
                                // 2 split (k_yfft, k_zsweep_fwd / k_zsweep_bwd)
     int cr_levels;             // slab kernel: cyclic-reduction levels before Thomas (0: Thomas with the table)
@@ -89,13 +91,14 @@ struct Work {
 struct UserPtrs {
     const double *in_u[kGridsPerLaunch], *in_v[kGridsPerLaunch], *in_w[kGridsPerLaunch], *in_p[kGridsPerLaunch];
     double *out_u[kGridsPerLaunch], *out_v[kGridsPerLaunch], *out_w[kGridsPerLaunch], *out_p[kGridsPerLaunch];
+    const double *in_q[kGridsPerLaunch];  // mass sources of Eq. (elliptic) (may be null)
     int g0, g1;                // grids [g0, g1) of this launch
     int blk0;                  // first block index (x-kernel numbering) of grid g0
 };
 
 // x-forward modes: right-hand side of the first solve, refinement residual (phi a
 // float-float pair), adjoint source, refinement residual of the first sweep (phi plain fp32)
-enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2, XM_RESID0 = 3 };
+enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2, XM_RESID0 = 3, XM_DIVQ = 4 /* XM_DIV with a mass source q */ };
 enum InvMode { IM_STORE = 0, IM_ACCUM = 1 };
 
 // Launchers (ibf_kernels.cu).  T = 0: fp64 path, 1: mixed path.

@@ -64,14 +64,16 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const ptrdiff_t pbase = (ptrdiff_t)k * plane;
     const int wall_x = W ? G.wall_x : 0, wall_y = W ? G.wall_y : 0, nxu = W ? G.nxu : nx;
 
+    // the first right-hand side (Eq. elliptic): (D u* - q)/(alpha dt), q = 0 in XM_DIV
+    constexpr bool DIVL = MODE == XM_DIV || MODE == XM_DIVQ;
     V cu, cv, cwp, cwm, cp;
-    if (MODE == XM_DIV) {
+    if (DIVL) {
         const double rhz = w.z.rhz[zo + k];
         cu = Coef<A>::c(rs * G.rdx);
         cv = Coef<A>::c(rs * G.rdy);
         cwp = Coef<A>::c(rs * rhz);
         cwm = cwp;
-        cp = A::zero();
+        cp = Coef<A>::c(-rs);
     } else if (MODE == XM_ADJ) {
         const double rhz = w.z.rhz[zo + k];
         cu = Coef<A>::c(rhz * G.rdx);
@@ -105,14 +107,16 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
         const bool own_up = (lane == 31) || (ii + 1 == nx);
         const bool own_dn = (lane == 0) || (ii == 0);
         const int spos = pos_nat(wall_x ? dct_perm(ii, nx) : ii, fN2);
-        if (MODE == XM_DIV || MODE == XM_ADJ) {
+        if (DIVL || MODE == XM_ADJ) {
             // wall-bounded x: u rows hold nx+1 faces; wall-bounded y: v planes hold ny+1 rows
             const double *u = p.in_u[gi] + (ptrdiff_t)k * ny * nxu;
             const double *vv = p.in_v[gi] + (ptrdiff_t)k * (W ? G.nyv : ny) * nx, *ww = p.in_w[gi] + pbase;
             // adjoint source: G^T skips wall faces (G is zero there)
             const bool zero_u = MODE == XM_ADJ && wall_x && ii == 0;
             const bool zero_un = MODE == XM_ADJ && wall_x && ii + 1 == nx;
-            const double *pp = (MODE == XM_ADJ && p.in_p[gi]) ? p.in_p[gi] + pbase : nullptr;
+            // extra cell-centred source: g_phi (adjoint) or the mass source q
+            const double *psrc = MODE == XM_ADJ ? p.in_p[gi] : (MODE == XM_DIVQ ? p.in_q[gi] : nullptr);
+            const double *pp = psrc ? psrc + pbase : nullptr;
             V vcur = A::zero();
             bool have_v = false;
             for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                         rvn[q] = __ldg(vv + jp * nx + ii);
                         rw0[q] = __ldg(ww + row + ii);
                         rw1[q] = __ldg(ww + plane + row + ii);
-                        if (MODE == XM_ADJ && pp) rp[q] = __ldg(pp + row + ii);
+                        if ((MODE == XM_ADJ || MODE == XM_DIVQ) && pp) rp[q] = __ldg(pp + row + ii);
                     }
                 }
                 if (need_v0) vcur = A::load(rv0);
@@ -159,18 +163,19 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                             if (wall_y && j + 1 == ny) Vn = A::zero();
                         }
                         V bv = A::add(A::mul(cu, A::sub(Un, U)), A::mul(cv, A::sub(Vn, Vc)));
-                        if (MODE == XM_DIV) {
+                        if (DIVL) {
                             bv = A::add(bv, A::mul(cwp, A::sub(W1, W0)));
+                            if (MODE == XM_DIVQ && pp) bv = A::add(bv, A::mul(cp, A::load(rp[q])));
                         } else {
                             bv = A::add(bv, A::sub(A::mul(cwp, W1), A::mul(cwm, W0)));
                             if (pp) bv = A::add(bv, A::mul(cp, A::load(rp[q])));
                         }
                         have_v = true;
                         if (act) {
-                            if (MODE == XM_DIV) vmax = fmaxf(vmax, absv<A>(bv));
+                            if (DIVL) vmax = fmaxf(vmax, absv<A>(bv));
                             if constexpr (sizeof(T) == 4)
                                 w.bdf[G.cell_off + pbase + row + i] = *reinterpret_cast<const float2 *>(&bv);
-                            else if (MODE == XM_DIV && w.bws)
+                            else if (DIVL && w.bws)
                                 w.bws[G.cell_off + pbase + row + i] = *reinterpret_cast<const double *>(&bv);
                             acc = A::add(acc, bv);
                             val = to_T<T, A>(bv) * scale;
@@ -235,7 +240,9 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                         float Pjp = pn[q], Pjm = Pm;
                         if (wall_y && j + 1 == ny) Pjp = Pc;
                         if (wall_y && j == 0) Pjm = Pc;
-                        const float Pkp = (k + 1 < nz) ? pkp[q] : Pc, Pkm = (k > 0) ? pkm[q] : Pc;
+                        // top: Neumann (difference zero) or Dirichlet outlet (phi = 0 on the face)
+                        const float Pkp = (k + 1 < nz) ? pkp[q] : (G.dir_top ? 0.f : Pc);
+                        const float Pkm = (k > 0) ? pkm[q] : Pc;
                         const df d2x = sum3(Pip, Pim, -2.f * Pc), d2y = sum3(Pjp, Pjm, -2.f * Pc);
                         const df dzp = two_sum(Pkp, -Pc), dzm = two_sum(Pc, -Pkm);
                         df lap = df_add(df_mul(cu, d2x), df_mul(cv, d2y));
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                         if (own_up) Pip = peu[q];
                         V Pim = shup(Pc, 1);
                         if (own_dn) Pim = ped[q];
-                        const V dzp = (k + 1 < nz) ? A::sub(pkp[q], Pc) : A::zero();
+                        const V dzp = (k + 1 < nz) ? A::sub(pkp[q], Pc) : (G.dir_top ? A::sub(A::zero(), Pc) : A::zero());
                         const V dzm = (k > 0) ? A::sub(Pc, pkm[q]) : A::zero();
                         // wall faces carry no gradient (Neumann phi)
                         const V dxp = (wall_x && ii + 1 == nx) ? A::zero() : A::sub(Pip, Pc);
@@ -334,14 +341,14 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     // of the right-hand side in the first pass; of phi in a refinement pass (k_00 forms
     // the plane means of the residual from both, since x and y differences sum to zero
     // over a plane)
-    if (MODE == XM_DIV || MODE == XM_ADJ) {
+    if (DIVL || MODE == XM_ADJ) {
         V tot = Red<A>::sum(acc, red);
         if (threadIdx.x == 0) w.partial[G.part_off + k * nrb + rb] = A::store(tot);
     } else {
         V totp = Red<A>::sum(acc_phi, red);
         if (threadIdx.x == 0) w.partial_phi[G.part_off + k * nrb + rb] = A::store(totp);
     }
-    if (MODE == XM_DIV) {
+    if (DIVL) {
         float mx = block_max(vmax, redf);
         if (threadIdx.x == 0) atomic_max_nonneg(w.maxb + g, (double)mx);
     }
@@ -403,6 +410,47 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const cx<T> *twx = reinterpret_cast<const cx<T> *>(w.twx) + G.twx_off;
     const int npair = rows >> 1;
     const int nload = ncb * npair * mb;
+    if (!(W && G.wall_x)) {
+        // real FFT input: the loads of kGather iterations are issued before any of
+        // their shared-memory stores (memory-level parallelism; the gather is
+        // latency-bound otherwise)
+        constexpr int kGather = 4;
+        const int nthr = blockDim.x;
+        for (int t0 = threadIdx.x; t0 < nload; t0 += kGather * nthr) {
+            cx<T> A_[kGather], B_[kGather];
+            int mq[kGather], sq[kGather];
+#pragma unroll
+            for (int u = 0; u < kGather; ++u) {
+                const int t = t0 + u * nthr;
+                A_[u] = B_[u] = {(T)0, (T)0};
+                mq[u] = -1;
+                sq[u] = 0;
+                if (t < nload) {
+                    const int rest = (int)fdiv((unsigned)t, fmb);
+                    const int mm = t - rest * mb;
+                    const int cb = (int)fdiv((unsigned)rest, fnpair);
+                    const int s_ = rest - cb * npair;
+                    const int m = cb * mb + mm;
+                    if (m < nxh) {
+                        mq[u] = m;
+                        sq[u] = s_;
+                        const int ja = j0 + 2 * s_, jb = ja + 1;
+                        if (ja < ny) A_[u] = spec[((size_t)cb * ny + ja) * mb + mm];
+                        if (jb < ny) B_[u] = spec[((size_t)cb * ny + jb) * mb + mm];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kGather; ++u) {
+                const int m = mq[u];
+                if (m < 0) continue;
+                cx<T> *seq = buf + sq[u] * sstride;
+                const cx<T> a = A_[u], bb = B_[u];
+                seq[pos_tr(m, N1, N2, fN1)] = {a.x - bb.y, a.y + bb.x};
+                if (m > 0 && 2 * m < nx) seq[pos_tr(nx - m, N1, N2, fN1)] = {a.x + bb.y, bb.x - a.y};
+            }
+        }
+    } else {
     for (int t = threadIdx.x; t < nload; t += blockDim.x) {
         const int rest = (int)fdiv((unsigned)t, fmb);
         const int mm = t - rest * mb;
@@ -415,8 +463,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
         if (ja < ny) A_ = spec[((size_t)cb * ny + ja) * mb + mm];
         if (jb < ny) B_ = spec[((size_t)cb * ny + jb) * mb + mm];
         cx<T> *seq = buf + s_ * sstride;
-        if (W && G.wall_x) {
-            // DCT-III input stage of two real coefficient rows a, b (real parts of the
+        {   // wall-bounded x: DCT-III input stage of two real coefficient rows a, b (real parts of the
             // spectrum): V_m = conj(W^m)(X_m - i X_{N-m}) per row, X_N = 0, packed as
             // V^a + i V^b; the unscaled inverse FFT then yields row a + i row b, reordered.
             T ac = (T)0, bc = (T)0;
@@ -429,10 +476,8 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
             const cx<T> Va = {tw.x * A_.x - tw.y * ac, -tw.x * ac - tw.y * A_.x};
             const cx<T> Vb = {tw.x * B_.x - tw.y * bc, -tw.x * bc - tw.y * B_.x};
             seq[pos_tr(m, N1, N2, fN1)] = {Va.x - Vb.y, Va.y + Vb.x};
-            continue;
         }
-        seq[pos_tr(m, N1, N2, fN1)] = {A_.x - B_.y, A_.y + B_.x};
-        if (m > 0 && 2 * m < nx) seq[pos_tr(nx - m, N1, N2, fN1)] = {A_.x + B_.y, B_.x - A_.y};
+    }
     }
     __syncthreads();
     fft_batch<T, +1>(buf, npair, sstride, N1, N2, fN1, fN2, twx);
@@ -479,7 +524,7 @@ constexpr int kRowGroupC = 2;
 //                    w_k = g_w,k + psi_{k-1} [k>=1] - psi_k [k<=nz-1].
 // PU: forward with a pressure update (pmode 1: p_n + phi, 2: minus cimp (b - <b>)).
 template <class A, int ADJ, bool W, bool PU>
-__global__ void __launch_bounds__(kXThreads, 4)
+__global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 4 : 3)  // fp64: room for the pressure terms
     k_correct(Work w, UserPtrs p, int use_ws, int lo_valid, double s, int pmode, double cimp) {
     typedef typename A::V V;
     const int b = blockIdx.x + p.blk0;
@@ -523,6 +568,8 @@ __global__ void __launch_bounds__(kXThreads, 4)
         cv = Coef<A>::c(s * G.rdy);
         cw = Coef<A>::c(s * w.z.rgzf[zo + k]);
     }
+    // outlet face coefficient (rgzf[nz] is 0 unless the top is a Dirichlet outlet)
+    const V cwt = Coef<A>::c(ADJ ? 0.0 : s * w.z.rgzf[zo + nz]);
     const int lane = threadIdx.x & 31;
     const SegMap sm = seg_map(nx, rows);
     for (int seg = sm.seg0; seg < sm.nseg; seg += sm.segstep) {
@@ -584,7 +631,8 @@ __global__ void __launch_bounds__(kXThreads, 4)
                     } else {
                         if (k == 0) wo[c] = rw[q];
                         else wo[c] = rw[q] + A::store(A::mul(cw, A::sub(pkm[q], Pc)));
-                        if (k == nz - 1) wo[c + plane] = rwt[q];
+                        if (k == nz - 1)  // outlet face: corrected with a Dirichlet outlet, else a wall
+                            wo[c + plane] = G.dir_top ? rwt[q] + A::store(A::mul(cwt, Pc)) : rwt[q];
                         if (po) {
                             if constexpr (!PU) {
                                 po[c] = A::store(A::norm(Pc));
@@ -646,6 +694,7 @@ __global__ void __launch_bounds__(kXThreads) k_divstat(Work w, UserPtrs p) {
     const double *u = p.out_u[gi] + (ptrdiff_t)k * ny * nxu, *vv = p.out_v[gi] + (ptrdiff_t)k * (W ? G.nyv : ny) * nx,
                  *ww = p.out_w[gi] + pbase;
     const V cu = Coef<A>::c(G.rdx), cv = Coef<A>::c(G.rdy), cw = Coef<A>::c(w.z.rhz[G.z_off + k]);
+    const double *qs = p.in_q[gi] ? p.in_q[gi] + pbase : nullptr;
     float mx = 0.f;
     const int ncell = min(rows, ny - j0) * nx;
     for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
@@ -657,6 +706,7 @@ __global__ void __launch_bounds__(kXThreads) k_divstat(Work w, UserPtrs p) {
         V d = A::mul(cu, A::sub(A::load(u[rowu + ip]), A::load(u[rowu + i])));
         d = A::add(d, A::mul(cv, A::sub(A::load(vv[jp * nx + i]), A::load(vv[row + i]))));
         d = A::add(d, A::mul(cw, A::sub(A::load(ww[plane + row + i]), A::load(ww[row + i]))));
+        if (qs) d = A::sub(d, A::load(qs[row + i]));  // constraint D u = q
         const float a = absv<A>(d);
         mx = (a > mx || a != a) ? a : mx;
     }
@@ -682,6 +732,8 @@ cudaError_t launch_xfwd_w(int mixed, int mode, const Work &w, const UserPtrs &p,
     if (mixed) {
         if (mode == XM_DIV)
             k_xfwd<float, DFArith, XM_DIV, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        else if (mode == XM_DIVQ)
+            k_xfwd<float, DFArith, XM_DIVQ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else if (mode == XM_RESID && !lo_valid)
             k_xfwd<float, DFArith, XM_RESID0, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else if (mode == XM_RESID)
@@ -691,6 +743,8 @@ cudaError_t launch_xfwd_w(int mixed, int mode, const Work &w, const UserPtrs &p,
     } else {
         if (mode == XM_DIV)
             k_xfwd<double, F64Arith, XM_DIV, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        else if (mode == XM_DIVQ)
+            k_xfwd<double, F64Arith, XM_DIVQ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else if (mode == XM_ADJ)
             k_xfwd<double, F64Arith, XM_ADJ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else
@@ -791,6 +845,7 @@ cudaError_t set_smem_limits(int mixed) {
         constexpr bool W = decltype(wtag)::value;
         if (mixed) {
             set((const void *)k_xfwd<float, DFArith, XM_DIV, W>);
+            set((const void *)k_xfwd<float, DFArith, XM_DIVQ, W>);
             set((const void *)k_xfwd<float, DFArith, XM_RESID, W>);
             set((const void *)k_xfwd<float, DFArith, XM_RESID0, W>);
             set((const void *)k_xfwd<float, DFArith, XM_ADJ, W>);
@@ -798,6 +853,7 @@ cudaError_t set_smem_limits(int mixed) {
             set((const void *)k_xinv<float, DFArith, IM_ACCUM, W>);
         } else {
             set((const void *)k_xfwd<double, F64Arith, XM_DIV, W>);
+            set((const void *)k_xfwd<double, F64Arith, XM_DIVQ, W>);
             set((const void *)k_xfwd<double, F64Arith, XM_ADJ, W>);
             set((const void *)k_xinv<double, F64Arith, IM_STORE, W>);
         }

@@ -99,6 +99,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
                                           const ibf_fields *out, double dt, double alpha, void *stream) {
     if (!grid || !opts || !in || !out) return IBF_ERR_INVALID_ARG;
     if (!in->u || !in->v || !in->w || !out->u || !out->v || !out->w || !out->p) return IBF_ERR_INVALID_ARG;
+    if (in->q) return IBF_ERR_INVALID_ARG;  // no mass source on this entry point
     if (!(dt > 0) || !(alpha > 0) || !std::isfinite(dt) || !std::isfinite(alpha)) return IBF_ERR_INVALID_ARG;
     if (opts->precision != IBF_FP64 && opts->precision != IBF_MIXED) return IBF_ERR_INVALID_ARG;
     if (opts->refine_steps < 0 || opts->refine_steps > 8 || opts->pressure != IBF_P_PHI) return IBF_ERR_INVALID_ARG;

@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(kSlabThreads) k_yzslab(Work w) {
                 *e = {(mm < nvalid) ? (T)s00[k] : (T)0, (T)0};
             } else {
                 const T a = az[k], c = cz[k];
-                Ar[t] = a; Cr[t] = c; Br[t] = -(a + c) + slab_lambda<T>(G, m, n);
+                const T ez = (k == nz - 1) ? (T)G.ez_top : (T)0;  // Dirichlet outlet (0 otherwise)
+                Ar[t] = a; Cr[t] = c; Br[t] = -(a + c) - ez + slab_lambda<T>(G, m, n);
             }
         }
         __syncthreads();
@@ -544,6 +545,7 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
         for (int k = threadIdx.x; k < nz; k += blockDim.x) {
             double lz = 0.0;
             if (k + 1 < nz) lz += w.z.cz[zo + k] * (Pk[k + 1] - Pk[k]);
+            else lz -= G.ez_top * Pk[k];  // Dirichlet outlet (ez_top = 0 with a Neumann top)
             if (k > 0) lz -= w.z.az[zo + k] * (Pk[k] - Pk[k - 1]);
             rhs[k] = rhs[k] - mb - lz;
         }
@@ -554,7 +556,8 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     // weighted mean of the phi being refined: the correction also removes it, so that
     // phi + delta keeps a zero weighted mean (L cannot see a constant)
     const double totp = first_solve ? 0.0 : Red<F64Arith>::sum(locp, red);
-    if (threadIdx.x == 0) red[0] = tot / G.sum_hz;
+    // a Dirichlet outlet makes the (0,0) system regular: nothing to remove
+    if (threadIdx.x == 0) red[0] = G.dir_top ? 0.0 : tot / G.sum_hz;
     __syncthreads();
     const double mean = red[0];
     if (threadIdx.x == 0 && first_solve) {
@@ -568,11 +571,13 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     // parallel cyclic reduction (Hockney 1965): each step eliminates from every row its
     // couplings at distance st; after ceil(log2 nz) steps row k reads phi_k = d_k / b_k.
     // Row k of L along z: a = az_k (to k-1), b = -(az_k + cz_k), c = cz_k (to k+1).
+    // With a Dirichlet outlet every row is regular (row nz-1 gains the outlet flux term).
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        if (k == 0) { A0[k] = 0.0; B0[k] = 1.0; C0[k] = 0.0; D0[k] = 0.0; }
+        if (k == 0 && !G.dir_top) { A0[k] = 0.0; B0[k] = 1.0; C0[k] = 0.0; D0[k] = 0.0; }
         else {
             const double a = w.z.az[zo + k], c = w.z.cz[zo + k];
-            A0[k] = a; B0[k] = -(a + c); C0[k] = (k == 0) ? 0.0 : c; D0[k] = rhs[k] - mean;
+            const double ez = (k == nz - 1) ? G.ez_top : 0.0;
+            A0[k] = a; B0[k] = -(a + c) - ez; C0[k] = c; D0[k] = rhs[k] - mean;
         }
     }
     __syncthreads();
@@ -608,7 +613,7 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     }
     __syncthreads();
     const double sv = Red<F64Arith>::sum(lsv, red);
-    if (threadIdx.x == 0) rhs[nz] = (sv + totp) / G.sum_hz;  // weighted mean to remove
+    if (threadIdx.x == 0) rhs[nz] = G.dir_top ? 0.0 : (sv + totp) / G.sum_hz;  // weighted mean to remove
     __syncthreads();
     const double mphi = rhs[nz];
     cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
@@ -649,7 +654,8 @@ __global__ void __launch_bounds__(256) k_build_table(Work w) {
         for (int k = 0; k < nz; ++k) {
             double inv = 0.0;
             if (valid) {
-                inv = 1.0 / (-(az[k] + cz[k]) + lam - az[k] * cp);
+                const double ez = (k == nz - 1) ? G.ez_top : 0.0;  // Dirichlet outlet (0 otherwise)
+                inv = 1.0 / (-(az[k] + cz[k]) - ez + lam - az[k] * cp);
                 cp = cz[k] * inv;
             }
             tab[((size_t)k * ncb + cb) * nslot + q] = (T)inv;

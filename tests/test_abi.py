@@ -64,7 +64,8 @@ def _plan(grid_kw, opts_kw=None, n=1):
     (dict(bc_x=2), N.IBF_ERR_UNSUPPORTED_BC),       # Dirichlet x
     (dict(bc_y=2), N.IBF_ERR_UNSUPPORTED_BC),       # Dirichlet y
     (dict(bc_x=1, nx=5), N.IBF_ERR_UNSUPPORTED_SIZE),  # wall-bounded x: same FFT sizes
-    (dict(bc_zhi=2), N.IBF_ERR_UNSUPPORTED_BC),
+    (dict(bc_zlo=2), N.IBF_ERR_UNSUPPORTED_BC),      # Dirichlet bottom
+    (dict(bc_zhi=0), N.IBF_ERR_UNSUPPORTED_BC),      # periodic z
     (dict(bc_zlo=7), N.IBF_ERR_INVALID_ARG),
     (dict(beta=-1.0), N.IBF_ERR_INVALID_ARG),
 ])

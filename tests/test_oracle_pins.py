@@ -360,3 +360,31 @@ def test_dirichlet_outlet_adjoint_matches_dense_transpose():
     ad, bd, cd = dp.project_T(gu, gv, gw, gp, dt=2e-3, alpha=0.5)
     for x, y in ((a, ad), (b, bd), (c, cd)):
         assert rel(x, y) < 1e-11
+
+
+# ---------------------------------------------------------------- mass source q (Eq. elliptic)
+def test_mass_source_closed_form_and_equivalence():
+    """u* = 0 with q = -alpha dt lam phi_e (phi_e a discrete eigenfunction) gives phi = phi_e and
+    u = -alpha dt G phi_e; and a source q = D e acts exactly like removing e from u*."""
+    nx, ny, nz, a, b, c = 12, 8, 10, 2, 1, 3
+    lx, ly, lz = 1.2, 0.8, 1.5
+    g = O.Grid(nx, ny, nz, lx=lx, ly=ly, lz=lz, beta=0.0)
+    i, j, k = np.arange(nx), np.arange(ny), np.arange(nz)
+    phi_e = (np.cos(math.pi * c * (k + 0.5) / nz)[:, None, None] * np.cos(2 * math.pi * b * j / ny)[None, :, None]
+             * np.cos(2 * math.pi * a * i / nx)[None, None, :])
+    lam = (_eig_lambda(a, nx, lx / nx, False) + _eig_lambda(b, ny, ly / ny, False)
+           + _eig_lambda(c, 2 * nz, lz / nz, False))
+    dt, alpha = 2e-3, 0.5
+    z = [np.zeros(s) for s in g.shapes]
+    phi, u, v, w, compat = O.project_q(g, *z, -alpha * dt * lam * phi_e, dt=dt, alpha=alpha)
+    assert rel(phi, phi_e) < TOL
+    gu, gv, gw = O.gradient(g, phi_e)
+    assert rel(u, -alpha * dt * gu) < 1e-11 and rel(w, -alpha * dt * gw) < 1e-11
+    # equivalence with a shifted velocity, on a stretched grid
+    g2 = O.Grid(8, 6, 7, lx=1.0, ly=0.7, lz=2.0, beta=2.0)
+    us = synth.uniform_velocity_np(81, 8, 6, 7)
+    e = synth.uniform_velocity_np(82, 8, 6, 7)
+    q = O.divergence(g2, *e)
+    phi_q, *_ = O.project_q(g2, *us, q, dt=dt, alpha=alpha)
+    phi_s, *_ = O.project(g2, *(x - y for x, y in zip(us, e)), dt=dt, alpha=alpha)
+    assert rel(phi_q, phi_s) < TOL
