@@ -44,8 +44,10 @@ BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of each
 # kernel from one ncu capture (512x512x128 mixed, see profiles/), valid while the
 # kernel sources hash to SOURCES_SHA256; otherwise the roofline's traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {}
-NCU_SOURCES_SHA256 = None
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.67, "x_forward_residual": 15.27, "correct": 64.69,
+                          "yz_forward": 8.42, "yz_backward": 8.43, "x_inverse_store": 6.57,
+                          "x_inverse_accumulate": 6.58}
+NCU_SOURCES_SHA256 = "106ce90aa4a73e759abd6ee307a02e02ee1f4c513c334e89dbf646147aebe65a"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_common.cuh", "ibf_device.cuh", "ibf_internal.h")
 
 
@@ -153,9 +155,10 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
-def time_steps(plan, ins, outs, K, W, ws):
+def time_steps(plan, ins, outs, K, W, ws, flush=None):
     """W warm-up then K timed projections; returns ms per step (CUDA events, max over ranks)
-    and the per-kernel profile over the timed steps."""
+    and the per-kernel profile over the timed steps.  With `flush` (a buffer larger than
+    L2) every step is timed alone, after the buffer has been rewritten outside its events."""
     import torch
     st = torch.cuda.current_stream()
     for _ in range(W):
@@ -165,41 +168,59 @@ def time_steps(plan, ins, outs, K, W, ws):
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(K):
-        plan.project_into([ins], [outs], DT, 1.0)
-    e1.record(st)
-    torch.cuda.synchronize()
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(K):
+            plan.project_into([ins], [outs], DT, 1.0)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+    else:
+        evs = []
+        for _ in range(K):
+            flush.add_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            plan.project_into([ins], [outs], DT, 1.0)
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / K
     barrier(ws)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / K
     prof = plan.profile_read(reset=True)
     plan.profile(False)
     return max_over_ranks(ms, ws), prof
 
 
-def cpu_baseline_child(nz_sample: int):
-    """Runs in a fresh process: the FP64 oracle on nx=ny=1024 with nz_sample levels."""
-    import numpy as np
+def workload_config(nx, ny, nz, refine):
+    return {"workload": f"{nx}x{ny}x{nz} staggered projection, periodic x,y (2pi), walls z in [0,2], "
+                        f"tanh beta {BETA}; velocity = k^-5/3 Fourier modes + U[-0.01,0.01] noise (seed {SEED}); "
+                        f"mixed precision (fp32 transforms/sweeps, float-float stencils, fp64 I/O), "
+                        f"{refine} refinement sweep(s)",
+            "grid": [nx, ny, nz], "refine_steps": refine}
+
+
+def cpu_baseline_child(spec: str):
+    """Runs in a fresh process: the FP64 oracle on an nx x ny x nz_sample slab of the workload."""
     from oracle import oracle as O
     from paper_2609_19130_gb300 import synth
-    n = 1024
-    g = O.Grid(n, n, nz_sample, lx=LX, ly=LY, lz=LZ, beta=BETA)
-    u, v, w = synth.uniform_velocity_np(SEED, n, n, nz_sample)
+    nx, ny, nz_sample = (int(x) for x in spec.split("x"))
+    g = O.Grid(nx, ny, nz_sample, lx=LX, ly=LY, lz=LZ, beta=BETA)
+    u, v, w = synth.uniform_velocity_np(SEED, nx, ny, nz_sample)
     O.lib()
     t0 = time.perf_counter()
     O.project(g, u, v, w, dt=DT)
     dt = time.perf_counter() - t0
-    cells = n * n * nz_sample
-    print(json.dumps({"seconds": dt, "cells": cells, "cores": os.cpu_count()}))
+    print(json.dumps({"seconds": dt, "cells": nx * ny * nz_sample, "cores": os.cpu_count()}))
 
 
-def run_cpu_baseline(nz_sample: int):
+def run_cpu_baseline(nx: int, ny: int, nz_sample: int):
     env = dict(os.environ)
     env["OMP_NUM_THREADS"] = str(os.cpu_count())
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", str(nz_sample)],
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", f"{nx}x{ny}x{nz_sample}"],
                        capture_output=True, text=True, env=env, timeout=900)
     line = [l for l in r.stdout.splitlines() if l.startswith("{")]
     if r.returncode != 0 or not line:
@@ -213,31 +234,81 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    nz_sample = args.ref_nz
+    nx, ny, nz = (int(x) for x in args.size.split("x"))
+    nz_sample = min(args.ref_nz, nz)
     times = []
     cores = None
     for i in range(args.warmup + args.steps):
-        res, err = run_cpu_baseline(nz_sample)
+        res, err = run_cpu_baseline(nx, ny, nz_sample)
         if res is None:
             print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + (err or "")[-200:]}))
             return 0
         cores = res["cores"]
         if i >= args.warmup:
             times.append(res["seconds"])
-    cells = 1024 * 1024 * nz_sample
+    cells = nx * ny * nz_sample
     sec = sum(times) / len(times)
     value = cells / sec
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"FP64 CPU oracle (naive DFT + Thomas), 1024x1024x{nz_sample} sample of the "
-                               f"1024x1024x512 stretched-z projection (beta {BETA})"},
+        "config": dict(workload_config(nx, ny, nz, args.refine), parallelism="host cores"),
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
-                         "sample": f"1024x1024x{nz_sample} cells per step, U[-1,1] velocity seed {SEED}"},
+                         "sample": f"FP64 oracle (naive DFT/DCT + Thomas) on {nx}x{ny}x{nz_sample} cells per step "
+                                   f"(the workload's planes, {nz_sample} z levels), U[-1,1] velocity seed {SEED}"},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+    return 0
+
+
+def bench_batch64(args):
+    """The batched workload: 64 uneven grids (nx, ny in {64,96,128,192}, nz in {64,128,256},
+    tanh beta in U[1,3], splitmix64 seed 1) projected by one plan, launch shapes autotuned;
+    one JSON line (not the headline, which is the single large grid)."""
+    import torch
+    from paper_2609_19130_gb300 import MIXED, Grid, Plan, synth
+    from paper_2609_19130_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    draws = synth.batch_grid_draws(1, 64)
+    grids = [Grid(nx, ny, nz, LX, LY, LZ, beta=b) for nx, ny, nz, b in draws]
+    ins, outs = [], []
+    for i, g in enumerate(grids):
+        u, v, w = synth.uniform_velocity_torch(1000 + i, g.nx, g.ny, g.nz, dev)
+        ins.append((u, v, w))
+        outs.append((torch.empty_like(u), torch.empty_like(v), torch.empty_like(w),
+                     torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device=dev)))
+    cells = sum(g.cells for g in grids)
+    plan = Plan(grids, precision=MIXED, refine_steps=args.refine, autotune=bool(args.autotune))
+    for _ in range(args.warmup):
+        plan.project_into(ins, outs, DT, 1.0)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev.index) as ck:
+        e0.record(st)
+        for _ in range(args.steps):
+            plan.project_into(ins, outs, DT, 1.0)
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    kinds = {}
+    for gi in range(len(grids)):
+        t = plan.tuning(gi)
+        key = {1: "streaming", 2: "slab", 3: "split"}[t["yz_kernel"]]
+        kinds[key] = kinds.get(key, 0) + 1
+    plan.close()
+    print(json.dumps({
+        "metric": "cells/s per batched pressure projection (64 uneven grids)", "value": cells / (ms * 1e-3),
+        "unit": "cells/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "64 grids, nx,ny in {64,96,128,192}, nz in {64,128,256}, beta U[1,3] (seed 1), "
+                               "U[-1,1] velocity (seed 1000+g)", "cells": cells, "refine_steps": args.refine,
+                   "autotuned": bool(args.autotune), "yz_kernels": kinds,
+                   "l2_policy": f"batch fields {cells * 56 / 1e9:.1f} GB > 129 MB L2: no flush"},
+        "clocks": ck.summary()}))
     return 0
 
 
@@ -256,13 +327,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--autotune", type=int, default=0, help="1: plan-time autotuning of the launch shapes")
     ap.add_argument("--tuning", default="", help="JSON dict of ibf_tuning fields forced for the mixed plan")
-    ap.add_argument("--cpu-child", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--batch64", action="store_true", help="time the 64-grid batched workload instead")
+    ap.add_argument("--cpu-child", default="", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_child:
         cpu_baseline_child(args.cpu_child)
         return 0
     if args.impl == "reference":
         return reference_arm(args)
+    if args.batch64:
+        return bench_batch64(args)
     if args.warmup < 3:
         args.warmup = 3
 
@@ -283,6 +357,11 @@ def main():
     torch.cuda.synchronize()
 
     hbm_peak, peak_kind = peaks()
+    # inputs + outputs of one step; below twice the 129 MB L2, flush it between timed steps
+    step_bytes = 8 * (sum(t.numel() for t in ins) + sum(t.numel() for t in outs))
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev) if step_bytes < (258 << 20) else None
+    l2_policy = (f"step fields {step_bytes / 1e9:.2f} GB > 2x the 129 MB L2: no flush between steps" if flush is None
+                 else "L2 flushed (256 MB written) before every timed step, outside its events")
     res = {}
     clocks = None
     for prec in ([MIXED] + ([] if args.no_fp64 else [FP64])):
@@ -291,7 +370,7 @@ def main():
                     autotune=bool(args.autotune), tuning=tun)
         if prec == MIXED:
             with Clocks(dev.index) as ck:
-                ms, prof = time_steps(plan, ins, outs, args.steps, args.warmup, ws)
+                ms, prof = time_steps(plan, ins, outs, args.steps, args.warmup, ws, flush)
             clocks = ck.summary()
             # diagnostics outside the timed region: divergence of the output
             (_, st) = plan.project_batch([ins], DT, out=[outs], stats=True)
@@ -299,7 +378,7 @@ def main():
             diag = {"max_div_out": float(st["max_div"][0]), "max_div_in": float(st["max_div_in"][0]),
                     "status": plan.sync_status()}
         else:
-            ms, prof = time_steps(plan, ins, outs, args.steps, args.warmup, ws)
+            ms, prof = time_steps(plan, ins, outs, args.steps, args.warmup, ws, flush)
             diag = None
         res[prec] = {"ms": ms, "prof": prof, "diag": diag, "plan": plan, "tuning": plan.tuning(0)}
 
@@ -326,13 +405,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{nx}x{ny}x{nz} staggered projection, periodic x,y (2pi), walls z in [0,2], "
-                               f"tanh beta {BETA}; velocity = k^-5/3 Fourier modes + U[-0.01,0.01] noise (seed {SEED}); "
-                               f"mixed precision (fp32 transforms/sweeps, float-float stencils, fp64 I/O), "
-                               f"{args.refine} refinement sweep(s)",
-                   "grid": [nx, ny, nz], "refine_steps": args.refine, "parallelism": "replicas" if ws > 1 else "1 GPU",
+        "config": dict(workload_config(nx, ny, nz, args.refine), **{
+                   "parallelism": "replicas" if ws > 1 else "1 GPU",
                    "launch_shape": mixed["tuning"], "autotuned": bool(args.autotune),
-                   "l2_policy": "inputs 4.3 GB per field (> 129 MB L2): no flush between steps"},
+                   "l2_policy": l2_policy}),
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                      "bytes_per_cell": BYTES_MIXED.get(dname, 0.0)},
@@ -351,47 +427,82 @@ def main():
                         "kernels": {k: {"launches": c, "ms_per_launch": t / c} for k, (c, t) in f["prof"].items()},
                         "speedup_mixed_over_fp64": f["ms"] / ms}
 
-    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    # End to end through the public API with host buffers (pinned), copies inside the timed
+    # region: every step uploads its own u*, v*, w* and downloads its own u, v, w, phi.  Steps
+    # are pipelined the way a caller streaming projections would run them: the upload of
+    # step i+1 and the download of step i run on their own streams while step i projects
+    # (device fields double-buffered; one pinned host set each way: uploads only read it and
+    # downloads are ordered on their stream; ordering by events).
     if not args.no_e2e:
         plan = mixed["plan"]
+        dev_sets = [(ins, outs), (tuple(torch.empty_like(t) for t in ins), tuple(torch.empty_like(t) for t in outs))]
         h_in = [t.cpu().pin_memory() for t in ins]
         h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
-        st = torch.cuda.current_stream()
+        s_comp = torch.cuda.current_stream()
+        s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
         h2d = sum(t.numel() * 8 for t in h_in)
         d2h = sum(t.numel() * 8 for t in h_out)
 
-        def e2e_step():
-            for d, h in zip(ins, h_in):
-                d.copy_(h, non_blocking=True)
-            plan.project_into([ins], [outs], DT, 1.0)
-            for h, d in zip(h_out, outs):
-                h.copy_(d, non_blocking=True)
+        def run_steps(n):
+            # buffer set b = i % 2; its inputs may be overwritten once step i-2 has projected,
+            # its outputs once step i-2 has been downloaded
+            projected = [None, None]
+            downloaded = [None, None]
+            for i in range(n):
+                b_ = i % 2
+                d_in, d_out = dev_sets[b_]
+                with torch.cuda.stream(s_up):
+                    if projected[b_] is not None:
+                        s_up.wait_event(projected[b_])
+                    for d, h in zip(d_in, h_in):
+                        d.copy_(h, non_blocking=True)
+                    up = torch.cuda.Event()
+                    up.record(s_up)
+                s_comp.wait_event(up)
+                if downloaded[b_] is not None:
+                    s_comp.wait_event(downloaded[b_])
+                plan.project_into([d_in], [d_out], DT, 1.0, stream=s_comp)
+                done = torch.cuda.Event()
+                done.record(s_comp)
+                projected[b_] = done
+                with torch.cuda.stream(s_down):
+                    s_down.wait_event(done)
+                    for h, d in zip(h_out, d_out):
+                        h.copy_(d, non_blocking=True)
+                    dn = torch.cuda.Event()
+                    dn.record(s_down)
+                    downloaded[b_] = dn
+            s_comp.wait_stream(s_down)
+            s_comp.wait_stream(s_up)
 
-        for _ in range(2):
-            e2e_step()
+        run_steps(2)
         torch.cuda.synchronize()
         barrier(ws)
-        ke = max(2, min(args.steps, 5))
+        ke = max(3, min(args.steps, 6))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(ke):
-            e2e_step()
-        e1.record(st)
+        e0.record(s_comp)
+        s_up.wait_stream(s_comp)
+        s_down.wait_stream(s_comp)
+        run_steps(ke)
+        e1.record(s_comp)
         torch.cuda.synchronize()
         ems = max_over_ranks(e0.elapsed_time(e1) / ke, ws)
         line["e2e"] = {"value": ws * cells / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ke}
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ke,
+                       "pipelined": "upload of step i+1 and download of step i overlap step i's projection"}
         line["gpu_launches"] += int(round(launches_per_step * ke))
+        del dev_sets, h_in, h_out
 
     for r in res.values():
         r["plan"].close()
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb, err = run_cpu_baseline(args.cpu_nz)
+        nzs = min(args.cpu_nz, nz)
+        cb, err = run_cpu_baseline(nx, ny, nzs)
         if cb is not None:
             line["cpu_baseline"] = {"value": cb["cells"] / cb["seconds"], "unit": "cells/s", "cores": cb["cores"],
                                     "kind": "oracle",
-                                    "sample": f"FP64 oracle on 1024x1024x{args.cpu_nz} (same planes, {args.cpu_nz} "
+                                    "sample": f"FP64 oracle on {nx}x{ny}x{nzs} (the workload's planes, {nzs} "
                                               f"z levels), {cb['seconds']:.1f} s"}
         else:
             line["cpu_baseline"] = {"value": None, "unit": "cells/s", "cores": os.cpu_count(), "kind": "oracle",
