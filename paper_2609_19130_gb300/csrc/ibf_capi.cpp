@@ -266,7 +266,10 @@ ibf_status resolve_tuning(const ibf_grid &g, int mixed, long long total_cols, in
         const int ny2 = g.ny / t->y_n1;
         const int mbmax = std::max(1, std::min(nxh, 4096 / g.ny));
         const int want = (64 + ny2 - 1) / ny2;
-        t->mb = (int)std::min<long long>(std::min(mbmax, want), std::max<long long>(1, total_cols / nsm));
+        // as few x-modes per block as keep every column block of the batch resident at
+        // once (one wave), but no more than 64 FFT tasks per pass need
+        const long long slots = (long long)(mixed ? kYZResidentF32 : kYZResidentF64) * nsm;
+        t->mb = (int)std::min<long long>(std::min(mbmax, want), std::max<long long>(1, (total_cols + slots - 1) / slots));
     }
     t->mb = std::min(t->mb, nxh);
     if (t->tri <= 0) t->tri = 1;

@@ -12,6 +12,9 @@ constexpr int kGridsPerLaunch = 32;
 constexpr int kXThreads = 256;   // x-direction (row) kernels and stencil kernels
 constexpr int kYZThreads = 128;  // y-FFT + z-tridiagonal column kernels
 constexpr int kYZStages = 2;     // planes in flight per column block in the yz kernels
+// CTAs of the streaming y/z kernels resident per SM (registers: fp32 kernels are capped at
+// 128 registers per thread; the fp64 ones use about 255)
+constexpr int kYZResidentF32 = 4, kYZResidentF64 = 2;
 constexpr int kSlabThreads = 256;  // resident-slab y/z kernel
 constexpr int kSweepThreads = 256; // split y/z path: Thomas sweeps, one thread per mode
 

@@ -145,7 +145,8 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     d.nyv = d.ny;
     const int mbmax = std::max(1, std::min(d.nxh, 4096 / d.ny));
     const int want = (64 + d.ny2 - 1) / d.ny2;
-    d.mb = std::min(std::min(mbmax, want), std::max(1, d.nxh / nsm));
+    const int slots = (mixed ? kYZResidentF32 : kYZResidentF64) * nsm;  // the rule of ibf_projection_plan
+    d.mb = std::min(std::min(mbmax, want), std::max(1, (d.nxh + slots - 1) / slots));
     d.ncb = (d.nxh + d.mb - 1) / d.mb;
     int rows = 2 * std::max(1, (mixed ? 8192 : 4096) / d.nx);
     rows = std::min(rows, (d.ny + 1) & ~1);

@@ -73,8 +73,10 @@ __device__ __forceinline__ void dct_pre(cx<T> *buf, int nseq, int sstride, int N
 // Shared memory: kYZStages x [FFT buffer (mb padded sequences) | pivot chunk], then the
 // Thomas state d'_{k-1} of every mode of the block.  Plane k+1 (spectrum and pivots)
 // is copied with cp.async while plane k is transformed and eliminated.
+// fp32: capped at 128 registers so that kYZResidentF32 CTAs fit on an SM (a few spilled
+// bytes cost less than the lost residency)
 template <typename T, bool W>
-__global__ void __launch_bounds__(kYZThreads) k_yzfwd(Work w) {
+__global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 1) k_yzfwd(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = find_grid(w.ystr_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
@@ -147,8 +149,9 @@ __global__ void __launch_bounds__(kYZThreads) k_yzfwd(Work w) {
 // Back substitution and inverse y-FFT of one column block, sweeping k = nz-1..0.
 // Shared memory: kYZStages x [d' chunk (slot order) | pivot chunk], then one FFT
 // buffer and the state phi_hat_{k+1}; plane k-1 is copied while plane k is processed.
+// fp32: capped at 128 registers (no spill) so that kYZResidentF32 CTAs fit on an SM
 template <typename T, bool W>
-__global__ void __launch_bounds__(kYZThreads) k_yzbwd(Work w) {
+__global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 1) k_yzbwd(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = find_grid(w.ystr_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
