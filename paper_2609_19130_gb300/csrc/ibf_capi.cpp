@@ -369,6 +369,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         d.inv_nxy = 1.0 / ((double)d.nx * d.ny);
         d.sum_hz = H.zf[d.nz] - H.zf[0];
         d.fnx = make_fdiv(d.nx);
+        d.fnph = make_fdiv(d.nx / 2 + 1);
         d.fnx1 = make_fdiv(d.nx1);
         d.fnx2 = make_fdiv(d.nx2);
         d.fny1 = make_fdiv(d.ny1);

@@ -17,6 +17,17 @@ __device__ __forceinline__ int find_grid(const int *start, int n, int b) {
     return lo;
 }
 
+// cp.async (sm_80+ asynchronous global->shared copy, L1-bypassing for 16 B) of one element
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem_src), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 template <class A> struct IsDF { static constexpr bool value = false; };
 template <> struct IsDF<DFArith> { static constexpr bool value = true; };
 

@@ -75,6 +75,72 @@ __device__ __forceinline__ df sum3(float a, float b, float c) {
     return two_sum(t.hi, __fadd_rn(t.lo, s.lo));
 }
 
+// the same sum as an unnormalised pair: hi the rounded sum, lo its error (rounded once)
+__device__ __forceinline__ df sum3u(float a, float b, float c) {
+    const df s = two_sum(a, b);
+    const df t = two_sum(s.hi, c);
+    return {t.hi, __fadd_rn(t.lo, s.lo)};
+}
+
+// c1 d1 + c2 d2 + c3 d3 of float-float operands as a normalised pair: each product
+// is its leading float and one FMA-collected error term (the lo x lo part, below
+// 2^-46 of the product, is dropped), the three leading floats are added without
+// error, and every error term is collected in one float that is added once at the
+// end (the compensated dot product of Ogita, Rump and Oishi, SIAM J. Sci. Comput.
+// 26 (2005), "Dot2", on float-float inputs).  Error below about 2^-45 of
+// |c1 d1| + |c2 d2| + |c3 d3|, as for a chain of df_mul / df_add.
+__device__ __forceinline__ df df_dot3(df c1, df d1, df c2, df d2, df c3, df d3) {
+    const float p1 = __fmul_rn(c1.hi, d1.hi);
+    float e1 = __fmaf_rn(c1.hi, d1.hi, -p1);
+    e1 = __fmaf_rn(c1.hi, d1.lo, e1);
+    e1 = __fmaf_rn(c1.lo, d1.hi, e1);
+    const float p2 = __fmul_rn(c2.hi, d2.hi);
+    float e2 = __fmaf_rn(c2.hi, d2.hi, -p2);
+    e2 = __fmaf_rn(c2.hi, d2.lo, e2);
+    e2 = __fmaf_rn(c2.lo, d2.hi, e2);
+    const float p3 = __fmul_rn(c3.hi, d3.hi);
+    float e3 = __fmaf_rn(c3.hi, d3.hi, -p3);
+    e3 = __fmaf_rn(c3.hi, d3.lo, e3);
+    e3 = __fmaf_rn(c3.lo, d3.hi, e3);
+    const df s = two_sum(p1, p2);
+    const df t = two_sum(s.hi, p3);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, s.lo)), t.lo);
+    return two_sum(t.hi, lo);
+}
+
+// b - c0 - (c1 d1 + c2 d2 + c3 d3 - c4 d4) as a normalised pair: products as in
+// df_dot3, the six leading floats added without error, one collected error term.
+__device__ __forceinline__ df df_resid4(df b, df c0, df c1, df d1, df c2, df d2, df c3, df d3, df c4, df d4) {
+    const float p1 = __fmul_rn(c1.hi, d1.hi);
+    float e1 = __fmaf_rn(c1.hi, d1.hi, -p1);
+    e1 = __fmaf_rn(c1.hi, d1.lo, e1);
+    e1 = __fmaf_rn(c1.lo, d1.hi, e1);
+    const float p2 = __fmul_rn(c2.hi, d2.hi);
+    float e2 = __fmaf_rn(c2.hi, d2.hi, -p2);
+    e2 = __fmaf_rn(c2.hi, d2.lo, e2);
+    e2 = __fmaf_rn(c2.lo, d2.hi, e2);
+    const float p3 = __fmul_rn(c3.hi, d3.hi);
+    float e3 = __fmaf_rn(c3.hi, d3.hi, -p3);
+    e3 = __fmaf_rn(c3.hi, d3.lo, e3);
+    e3 = __fmaf_rn(c3.lo, d3.hi, e3);
+    const float p4 = __fmul_rn(c4.hi, d4.hi);
+    float e4 = __fmaf_rn(c4.hi, d4.hi, -p4);
+    e4 = __fmaf_rn(c4.hi, d4.lo, e4);
+    e4 = __fmaf_rn(c4.lo, d4.hi, e4);
+    df s = two_sum(b.hi, -c0.hi);
+    float lo = __fadd_rn(__fsub_rn(b.lo, c0.lo), s.lo);
+    s = two_sum(s.hi, -p1);
+    lo = __fadd_rn(lo, s.lo);
+    s = two_sum(s.hi, -p2);
+    lo = __fadd_rn(lo, s.lo);
+    s = two_sum(s.hi, -p3);
+    lo = __fadd_rn(lo, s.lo);
+    s = two_sum(s.hi, p4);
+    lo = __fadd_rn(lo, s.lo);
+    lo = __fadd_rn(lo, __fsub_rn(__fsub_rn(e4, e1), __fadd_rn(e2, e3)));
+    return two_sum(s.hi, lo);
+}
+
 // fp64 -> df32 without fp64 arithmetic.  hi takes the sign, the exponent and the
 // top 23 fraction bits (truncated); lo = x - hi is formed from the remaining 29
 // bits (rounded to 24 by the integer->float conversion), so hi + lo == x within

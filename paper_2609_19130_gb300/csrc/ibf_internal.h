@@ -48,7 +48,7 @@ struct GridDev {
     double dx, dy, rdx, rdy;   // spacings and their inverses
     double inv_nxy;            // 1 / (nx ny)
     double sum_hz;             // lz
-    FDiv fnx, fnx1, fnx2, fny1, fny2, fmb, frows, fnpair;
+    FDiv fnx, fnx1, fnx2, fny1, fny2, fmb, frows, fnpair, fnph;  // fnph: nx/2 + 1
 };
 
 // Per-level arrays (index z_off + k; nz+1 entries per grid, the last one only used where noted).

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
             const double *psrc = MODE == XM_ADJ ? p.in_p[gi] : (MODE == XM_DIVQ ? p.in_q[gi] : nullptr);
             const double *pp = psrc ? psrc + pbase : nullptr;
             V vcur = A::zero();
+            double vcur64 = 0.0;  // float-float divergence: v of the current row, fp64
             bool have_v = false;
             for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
                 // load phase: every fp64 input of up to kRowGroup rows is requested first
@@ -141,7 +142,10 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                         if ((MODE == XM_ADJ || MODE == XM_DIVQ) && pp) rp[q] = __ldg(pp + row + ii);
                     }
                 }
-                if (need_v0) vcur = A::load(rv0);
+                if (need_v0) {
+                    if constexpr (IsDF<A>::value && DIVL) vcur64 = rv0;
+                    else vcur = A::load(rv0);
+                }
 #pragma unroll
                 for (int q = 0; q < kRowGroup; ++q) {
                     const int jl = jg + q, j = j0 + jl;
@@ -149,6 +153,19 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                     T val = (T)0;
                     if (j < ny) {
                         const int row = j * nx;
+                        V bv;
+                        if constexpr (IsDF<A>::value && DIVL) {
+                            // the three face differences in fp64 (three DADD per cell, each
+                            // rounded to 2^-53 of the difference), then the coefficient
+                            // products and their sum in float-float
+                            double Un = __shfl_down_sync(0xffffffffu, ru[q], 1);
+                            if (own_up) Un = rue[q];
+                            const double Vc = vcur64;
+                            vcur64 = rvn[q];
+                            bv = df_dot3(cu, f64_to_df(__dsub_rn(Un, ru[q])), cv, f64_to_df(__dsub_rn(rvn[q], Vc)),
+                                         cwp, f64_to_df(__dsub_rn(rw1[q], rw0[q])));
+                            if (MODE == XM_DIVQ && pp) bv = A::add(bv, A::mul(cp, A::load(rp[q])));
+                        } else {
                         V U = A::load(ru[q]);
                         V Un = shdown(U, 1);
                         if (own_up) Un = A::load(rue[q]);
@@ -162,13 +179,14 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                             if (wall_y && j == 0) Vc = A::zero();
                             if (wall_y && j + 1 == ny) Vn = A::zero();
                         }
-                        V bv = A::add(A::mul(cu, A::sub(Un, U)), A::mul(cv, A::sub(Vn, Vc)));
+                        bv = A::add(A::mul(cu, A::sub(Un, U)), A::mul(cv, A::sub(Vn, Vc)));
                         if (DIVL) {
                             bv = A::add(bv, A::mul(cwp, A::sub(W1, W0)));
                             if (MODE == XM_DIVQ && pp) bv = A::add(bv, A::mul(cp, A::load(rp[q])));
                         } else {
                             bv = A::add(bv, A::sub(A::mul(cwp, W1), A::mul(cwm, W0)));
                             if (pp) bv = A::add(bv, A::mul(cp, A::load(rp[q])));
+                        }
                         }
                         have_v = true;
                         if (act) {
@@ -243,12 +261,10 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
                         // top: Neumann (difference zero) or Dirichlet outlet (phi = 0 on the face)
                         const float Pkp = (k + 1 < nz) ? pkp[q] : (G.dir_top ? 0.f : Pc);
                         const float Pkm = (k > 0) ? pkm[q] : Pc;
-                        const df d2x = sum3(Pip, Pim, -2.f * Pc), d2y = sum3(Pjp, Pjm, -2.f * Pc);
+                        const df d2x = sum3u(Pip, Pim, -2.f * Pc), d2y = sum3u(Pjp, Pjm, -2.f * Pc);
                         const df dzp = two_sum(Pkp, -Pc), dzm = two_sum(Pc, -Pkm);
-                        df lap = df_add(df_mul(cu, d2x), df_mul(cv, d2y));
-                        lap = df_add(lap, df_sub(df_mul(cwp, dzp), df_mul(cwm, dzm)));
                         if (act) {
-                            const df bv = df_sub(df_sub(df{bdv[q].x, bdv[q].y}, cp), lap);
+                            const df bv = df_resid4(df{bdv[q].x, bdv[q].y}, cp, cu, d2x, cv, d2y, cwp, dzp, cwm, dzm);
                             acc_phi = df_addf(acc_phi, Pc);
                             val = df_to_f(bv) * scale;
                         }
@@ -411,44 +427,45 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const int npair = rows >> 1;
     const int nload = ncb * npair * mb;
     if (!(W && G.wall_x)) {
-        // real FFT input: the loads of kGather iterations are issued before any of
-        // their shared-memory stores (memory-level parallelism; the gather is
-        // latency-bound otherwise)
-        constexpr int kGather = 4;
-        const int nthr = blockDim.x;
-        for (int t0 = threadIdx.x; t0 < nload; t0 += kGather * nthr) {
-            cx<T> A_[kGather], B_[kGather];
-            int mq[kGather], sq[kGather];
-#pragma unroll
-            for (int u = 0; u < kGather; ++u) {
-                const int t = t0 + u * nthr;
-                A_[u] = B_[u] = {(T)0, (T)0};
-                mq[u] = -1;
-                sq[u] = 0;
-                if (t < nload) {
-                    const int rest = (int)fdiv((unsigned)t, fmb);
-                    const int mm = t - rest * mb;
-                    const int cb = (int)fdiv((unsigned)rest, fnpair);
-                    const int s_ = rest - cb * npair;
-                    const int m = cb * mb + mm;
-                    if (m < nxh) {
-                        mq[u] = m;
-                        sq[u] = s_;
-                        const int ja = j0 + 2 * s_, jb = ja + 1;
-                        if (ja < ny) A_[u] = spec[((size_t)cb * ny + ja) * mb + mm];
-                        if (jb < ny) B_[u] = spec[((size_t)cb * ny + jb) * mb + mm];
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kGather; ++u) {
-                const int m = mq[u];
-                if (m < 0) continue;
-                cx<T> *seq = buf + sq[u] * sstride;
-                const cx<T> a = A_[u], bb = B_[u];
-                seq[pos_tr(m, N1, N2, fN1)] = {a.x - bb.y, a.y + bb.x};
-                if (m > 0 && 2 * m < nx) seq[pos_tr(nx - m, N1, N2, fN1)] = {a.x + bb.y, bb.x - a.y};
-            }
+        // real FFT input Z = X_a + i X_b of the row pair (a, b): Z_m = A_m + i B_m and
+        // Z_{nx-m} = conj(A_m) + i conj(B_m).  Every spectrum value is first copied
+        // asynchronously straight to shared memory (the whole block's input in flight at
+        // once): A_m to the slot of Z_m, B_m to the slot of Z_{nx-m}, or, where that is
+        // Z_m itself (m = 0, m = nx/2), to a padding slot of the sequence (N2: the pad
+        // column of row 0; N1 (N2+1): the pad after the last row).  A pass over the
+        // pairs (m, nx-m) then forms Z in place.
+        const int seqlen = fft_seq_len(N1, N2);
+        for (int t = threadIdx.x; t < nload; t += blockDim.x) {
+            const int rest = (int)fdiv((unsigned)t, fmb);
+            const int mm = t - rest * mb;
+            const int cb = (int)fdiv((unsigned)rest, fnpair);
+            const int s_ = rest - cb * npair;
+            const int m = cb * mb + mm;
+            if (m >= nxh) continue;
+            cx<T> *seq = buf + s_ * sstride;
+            cx<T> *da = seq + pos_tr(m, N1, N2, fN1);
+            cx<T> *db = seq + (m == 0 ? N2 : (2 * m == nx ? seqlen : pos_tr(nx - m, N1, N2, fN1)));
+            const int ja = j0 + 2 * s_, jb = ja + 1;
+            const cx<T> *src = spec + ((size_t)cb * ny + ja) * mb + mm;
+            if (ja < ny) cp_async<sizeof(cx<T>)>(da, src);
+            else *da = {(T)0, (T)0};
+            if (jb < ny) cp_async<sizeof(cx<T>)>(db, src + mb);
+            else *db = {(T)0, (T)0};
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        const int npm = nx / 2 + 1;  // pairs (m, nx-m), m = 0..nx/2
+        const FDiv fnph = G.fnph;
+        for (int t = threadIdx.x; t < npair * npm; t += blockDim.x) {
+            const int s_ = (int)fdiv((unsigned)t, fnph), m = t - s_ * npm;
+            cx<T> *seq = buf + s_ * sstride;
+            const int pa = pos_tr(m, N1, N2, fN1);
+            const bool self = m == 0 || 2 * m == nx;
+            const int pb = m == 0 ? N2 : (2 * m == nx ? seqlen : pos_tr(nx - m, N1, N2, fN1));
+            const cx<T> a = seq[pa], bb = seq[pb];
+            seq[pa] = {a.x - bb.y, a.y + bb.x};
+            if (!self) seq[pb] = {a.x + bb.y, bb.x - a.y};
         }
     } else {
     for (int t = threadIdx.x; t < nload; t += blockDim.x) {

@@ -157,6 +157,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     d.inv_nxy = 1.0 / ((double)d.nx * d.ny);
     d.sum_hz = g.lz;
     d.fnx = fdiv_of(d.nx); d.fnx1 = fdiv_of(d.nx1); d.fnx2 = fdiv_of(d.nx2);
+    d.fnph = fdiv_of(d.nx / 2 + 1);
     d.fny1 = fdiv_of(d.ny1); d.fny2 = fdiv_of(d.ny2);
     d.fmb = fdiv_of(d.mb); d.frows = fdiv_of(d.rows); d.fnpair = fdiv_of(d.rows / 2);
     const size_t cells = (size_t)d.nx * d.ny * nz;

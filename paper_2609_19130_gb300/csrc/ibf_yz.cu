@@ -13,17 +13,6 @@ template <typename T> __device__ __forceinline__ const T *zarr(const double *d, 
 template <> __device__ __forceinline__ const double *zarr<double>(const double *d, const float *) { return d; }
 template <> __device__ __forceinline__ const float *zarr<float>(const double *, const float *f) { return f; }
 
-// cp.async (sm_80+ asynchronous global->shared copy, L1-bypassing for 16 B) of one element
-template <int BYTES> __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem_src), "n"(BYTES));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
 // DCT-II post-twiddle of the FFT V (in place, FFT output order) of every Makhoul-
 // reordered sequence of a column block: with P = W^n V_n, Q = conj(W^n) V_{N-n},
 // W = exp(-i pi/(2N)), the coefficients are X_n = (P + Q)/2 and X_{N-n} = i (P - Q)/2
