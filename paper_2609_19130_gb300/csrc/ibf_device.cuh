@@ -165,48 +165,32 @@ __device__ __forceinline__ df f64_to_df(double x) {
     return {__uint_as_float(s | hbits), lo};
 }
 
-// fp32 -> fp64 bit pattern without F2F (fp32 denormals flush to signed zero).
-__device__ __forceinline__ double f32_to_f64(float f) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xFFu;
-    const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
-    if (e == 0u) return __longlong_as_double((long long)s);
-    unsigned long long E = (e == 0xFFu) ? 0x7FFull : (unsigned long long)(e + 896u);
-    unsigned long long M = (unsigned long long)(b & 0x7FFFFFu) << 29;
-    return __longlong_as_double((long long)(s | (E << 52) | M));
-}
-
 // df32 -> fp64 without fp64 arithmetic.  For a normalised pair (|lo| <= ulp(hi),
-// which every df_* operation returns) hi + lo is exactly an fp64 number in hi's
-// binade, so it is hi's fp64 bit pattern plus lo's significand aligned to hi's fp64
-// ulp (at most 2^29, so 32-bit arithmetic suffices); the only binade change
-// possible is a borrow below a power of two (hi's fraction zero, lo of opposite
-// sign), where the ulp halves.  lo bits below 2^-52 of hi are truncated.
+// which every df_* operation returns; hi = 0 implies lo = 0) hi + lo is exactly an
+// fp64 number in hi's binade, so it is hi's fp64 bit pattern plus lo's significand
+// aligned to hi's fp64 ulp (a shift by el - eh + 29 <= 6, so 32-bit arithmetic
+// suffices); the only binade change possible is a borrow below a power of two (hi's
+// fraction zero, lo of opposite sign), where the ulp halves.  lo bits below 2^-52 of
+// hi are truncated, a subnormal lo (|hi| below 2^-102) is dropped.  hi zero or
+// subnormal gives a signed zero; hi inf / nan stays inf / nan.
 __device__ __forceinline__ double df_to_f64(df a) {
     const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
-    const unsigned ha = hb & 0x7FFFFFFFu;
-    if (ha == 0u) return f32_to_f64(a.lo);                  // hi zero: lo carries the value
-    // hi as fp64: sign, exponent + 896, fraction << 29 (hi normal and finite)
-    unsigned hw = (hb & 0x80000000u) | ((ha >> 3) + 0x38000000u);
-    unsigned lw = hb << 29;
-    if (ha < 0x00800000u || ha >= 0x7F800000u) return f32_to_f64(a.hi);  // subnormal / inf / nan
+    const unsigned ha = hb & 0x7FFFFFFFu, sgn = hb & 0x80000000u;
+    const bool special = ha >= 0x7F800000u;
+    // hi as fp64: sign, exponent + 896 (all ones for inf / nan), fraction << 29
+    const unsigned hw = sgn | ((ha >> 3) + 0x38000000u) | (special ? 0x7FF00000u : 0u);
+    const unsigned lw = hb << 29;
     const unsigned el = (lb >> 23) & 0xFFu;
-    if (el != 0u) {
-        const unsigned L = (1u << 23) | (lb & 0x7FFFFFu);
-        const int sh = (int)el - (int)(ha >> 23) + 29;           // <= 5 for a normalised pair
-        unsigned Li = 0u;
-        if (sh >= 0) Li = L << min(sh, 8);
-        else if (sh > -24) Li = L >> (-sh);
-        unsigned long long H = ((unsigned long long)hw << 32) | lw;
-        if ((hb ^ lb) & 0x80000000u) {
-            if ((ha & 0x7FFFFFu) == 0u) Li <<= 1;
-            H -= Li;
-        } else {
-            H += Li;
-        }
-        return __longlong_as_double((long long)H);
-    }
-    return __longlong_as_double((long long)(((unsigned long long)hw << 32) | lw));
+    const int sh = (int)el - (int)(ha >> 23) + 29;
+    // L 2^sh with the bits below 2^0 truncated (shift amounts of 32 and more give 0)
+    unsigned Li = __funnelshift_rc(((lb & 0x7FFFFFu) | 0x800000u) << 8, 0u, (unsigned)(8 - sh));
+    if (el == 0u || special) Li = 0u;
+    const bool neg = ((hb ^ lb) & 0x80000000u) != 0u;
+    if (neg && (ha & 0x7FFFFFu) == 0u) Li <<= 1;
+    unsigned long long H = ((unsigned long long)hw << 32) | lw;
+    H = neg ? H - Li : H + Li;
+    if (ha < 0x00800000u) H = (unsigned long long)sgn << 32;
+    return __longlong_as_double((long long)H);
 }
 
 // ------------------------------------------------------------------ precision policies
