@@ -378,6 +378,26 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + (size_t)k * ncb * ny * mb;
     const int nout = ncb * rows * mb;
     const FDiv fmb = G.fmb, frows = G.frows;
+    if (mb == 1 && kXThreads % rows == 0 && !wall_x) {
+        // one x-mode per column block: every thread keeps one row jl and steps through
+        // the modes m0, m0 + kXThreads / rows, ... (the rows of one mode are contiguous
+        // in the spectrum, so consecutive threads store consecutive elements)
+        const int m0 = (int)fdiv((unsigned)threadIdx.x, frows), mstep = kXThreads / rows;
+        const int jl = threadIdx.x - m0 * rows, j = j0 + jl;
+        if (j < ny) {
+            const cx<T> *seq = buf + (jl >> 1) * sstride;
+            cx<T> *dst = spec + j;
+            const bool odd = (jl & 1) != 0;
+            for (int m = m0; m < nxh; m += mstep) {
+                const cx<T> Zm = seq[pos_tr(m, N1, N2, fN1)];
+                const cx<T> Zc = seq[pos_tr(m == 0 ? 0 : nx - m, N1, N2, fN1)];
+                const cx<T> X = odd ? cx<T>{(Zm.y + Zc.y) * (T)0.5, (Zc.x - Zm.x) * (T)0.5}
+                                    : cx<T>{(Zm.x + Zc.x) * (T)0.5, (Zm.y - Zc.y) * (T)0.5};
+                dst[(size_t)m * ny] = X;
+            }
+        }
+        return;
+    }
     for (int t = threadIdx.x; t < nout; t += blockDim.x) {
         const int rest = (int)fdiv((unsigned)t, fmb);
         const int mm = t - rest * mb;
