@@ -178,13 +178,22 @@ FDiv make_fdiv(unsigned d) {
 }
 
 // exp(-2 pi i r / n), r < n, in fp64 (host libm)
-void twiddles(int n, std::vector<double> &out) {
-    out.resize(2 * (size_t)n);
-    for (int r = 0; r < n; ++r) {
-        const double a = 2.0 * M_PI * (double)r / (double)n;
-        out[2 * r] = std::cos(a);
-        out[2 * r + 1] = -std::sin(a);
-    }
+// Four-step twiddles w^(a b), w = exp(-2 pi i / n), of an n = n1 n2 FFT, in the two
+// layouts their passes read with consecutive lanes on consecutive entries: forward
+// F[q n2 + c] = w^(q c) (q < n1, c < n2; the column pass, lanes over columns c), then
+// inverse I[p n1 + q1] = w^(p q1) (p < n2, q1 < n1; the row pass, lanes over rows q1).
+void twiddles(int n, int n1, std::vector<double> &out) {
+    const int n2 = n / n1;
+    out.resize(4 * (size_t)n);
+    auto put = [&](size_t i, long long e) {
+        const double a = 2.0 * M_PI * (double)(e % n) / (double)n;
+        out[2 * i] = std::cos(a);
+        out[2 * i + 1] = -std::sin(a);
+    };
+    for (int q = 0; q < n1; ++q)
+        for (int c = 0; c < n2; ++c) put((size_t)q * n2 + c, (long long)q * c);
+    for (int p = 0; p < n2; ++p)
+        for (int q1 = 0; q1 < n1; ++q1) put((size_t)n + (size_t)p * n1 + q1, (long long)p * q1);
 }
 
 // exp(-i pi m / (2n)), m < n: the DCT-II post-twiddles (Makhoul)
@@ -333,10 +342,10 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         d.part_off = poff;
         poff += d.nz * d.nrb;
         d.twx_off = (int)(twx_all.size() / 2);
-        twiddles(d.nx, tmp);
+        twiddles(d.nx, d.nx1, tmp);
         twx_all.insert(twx_all.end(), tmp.begin(), tmp.end());
         d.twy_off = (int)(twy_all.size() / 2);
-        twiddles(d.ny, tmp);
+        twiddles(d.ny, d.ny1, tmp);
         twy_all.insert(twy_all.end(), tmp.begin(), tmp.end());
         d.dctx_off = (int)(twx_all.size() / 2);
         if (d.wall_x) {

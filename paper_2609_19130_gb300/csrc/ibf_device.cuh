@@ -351,7 +351,10 @@ template <typename T, int N, int OFF, int STRIDE, int DIR> struct IPDFT<T, N, 4,
 //             output X[q] at (q % N1, q / N1)  ["transposed"]
 //   inverse:  input at the transposed positions, row pass (DFT_N2^-1), multiply by
 //             w_N^-(p2 q1), column pass (DFT_N1^-1); output natural, unnormalised.
-// tw[r] = exp(-2 pi i r / N), r < N (global memory, read through the L1 cache).
+// tw: the four-step twiddles w_N^(a b), w_N = exp(-2 pi i / N), as two tables laid out
+// so that the lanes of a pass read consecutive entries: forward F[q1 N2 + p2] (column
+// pass, lanes over columns p2), then inverse I[p2 N1 + q1] at tw + N (row pass, lanes
+// over rows q1).  Global memory, read through the L1 cache.
 __host__ __device__ __forceinline__ int fft_pos_nat(int p, int N2) { return (p / N2) * (N2 + 1) + (p % N2); }
 __host__ __device__ __forceinline__ int fft_pos_tr(int q, int N1, int N2) { return (q % N1) * (N2 + 1) + (q / N1); }
 __host__ __device__ __forceinline__ int fft_seq_len(int N1, int N2) { return N1 * (N2 + 1); }
@@ -382,25 +385,27 @@ __device__ __forceinline__ void ip_store(cx<T> (&x)[P], cx<T> *base, int ld, con
     }
 }
 
-// column task: DFT_N1 down column c of one sequence (P == N1); forward multiplies by w_N^(c q1)
+// column task: DFT_N1 down column c of one sequence (P == N1); forward multiplies output
+// q1 by w_N^(q1 c) = F[q1 N2 + c] (ld = N2 + 1)
 template <typename T, int P, int DIR>
 __device__ __forceinline__ void fft_col_task(cx<T> *seq, int c, int ld, const cx<T> *tw) {
     cx<T> x[P];
 #pragma unroll
     for (int r = 0; r < P; ++r) x[r] = seq[r * ld + c];
     IPDFT<T, P, P, 0, 1, DIR>::run(x);
-    if (DIR < 0 && c > 0) ip_store<T, P, 0, true, false>(x, seq + c, ld, tw, c);
+    if (DIR < 0 && c > 0) ip_store<T, P, 0, true, false>(x, seq + c, ld, tw + c, ld - 1);
     else ip_store<T, P, 0, false, false>(x, seq + c, ld, tw, 0);
 }
-// row task: DFT_N2 along row q1 of one sequence (P == N2); inverse then multiplies by w_N^-(p2 q1)
+// row task: DFT_N2 along row q1 of one sequence (P == N2); inverse then multiplies output
+// p2 by w_N^-(p2 q1) = conj(I[p2 N1 + q1]), I at tw + N1 N2
 template <typename T, int P, int DIR>
-__device__ __forceinline__ void fft_row_task(cx<T> *seq, int q1, int ld, const cx<T> *tw) {
+__device__ __forceinline__ void fft_row_task(cx<T> *seq, int q1, int ld, const cx<T> *tw, int N1) {
     cx<T> x[P];
     cx<T> *row = seq + q1 * ld;
 #pragma unroll
     for (int c = 0; c < P; ++c) x[c] = row[c];
     IPDFT<T, P, P, 0, 1, DIR>::run(x);
-    if (DIR > 0 && q1 > 0) ip_store<T, P, 0, true, true>(x, row, 1, tw, q1);
+    if (DIR > 0 && q1 > 0) ip_store<T, P, 0, true, true>(x, row, 1, tw + N1 * P + q1, N1);
     else ip_store<T, P, 0, false, false>(x, row, 1, tw, 0);
 }
 
@@ -421,7 +426,7 @@ __device__ __forceinline__ void fft_row_pass_P(cx<T> *buf, int nseq, int sstride
     const int ntask = nseq * N1;
     for (int t = tid; t < ntask; t += nthr) {
         const int s = (int)fdiv((unsigned)t, fN1), q1 = t - s * N1;
-        fft_row_task<T, P, DIR>(buf + s * sstride, q1, N2 + 1, tw);
+        fft_row_task<T, P, DIR>(buf + s * sstride, q1, N2 + 1, tw, N1);
     }
 }
 

@@ -184,7 +184,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     const size_t o_hz = cv.take(L * 8), o_rhz = cv.take(L * 8), o_rgzf = cv.take(L * 8), o_az = cv.take(L * 8),
                  o_cz = cv.take(L * 8), o_inv00 = cv.take(L * 8), o_azf = cv.take(L * 4), o_czf = cv.take(L * 4),
                  o_rhzdf = cv.take(L * 8), o_rgzfdf = cv.take(L * 8);
-    const size_t o_twx = cv.take(csz * d.nx), o_twy = cv.take(csz * d.ny);
+    const size_t o_twx = cv.take(csz * 2 * d.nx), o_twy = cv.take(csz * 2 * d.ny);
     const size_t upload_bytes = cv.off;
     const size_t o_spec = cv.take(csz * nspec), o_tab = cv.take(rsz * nspec);
     const size_t o_bdf = mixed ? cv.take(8 * cells) : 0;
@@ -232,15 +232,22 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     put(o_az, az.data(), L * 8); put(o_cz, cz.data(), L * 8); put(o_inv00, inv00.data(), L * 8);
     put(o_azf, azf.data(), L * 4); put(o_czf, czf.data(), L * 4);
     put(o_rhzdf, rhzdf.data(), L * 8); put(o_rgzfdf, rgzfdf.data(), L * 8);
-    auto tw = [&](size_t o, int n) {  // exp(-2 pi i r / n) in the solve precision
-        for (int r = 0; r < n; ++r) {
-            const double a = 2.0 * M_PI * (double)r / (double)n, c = std::cos(a), sn = -std::sin(a);
-            if (mixed) { const float v[2] = {(float)c, (float)sn}; put(o + 8 * (size_t)r, v, 8); }
-            else { const double v[2] = {c, sn}; put(o + 16 * (size_t)r, v, 16); }
-        }
+    // four-step twiddles w^(a b), w = exp(-2 pi i / n), in the solve precision: forward
+    // table F[q n2 + c] = w^(q c), then inverse table I[p n1 + q1] = w^(p q1)
+    auto tw = [&](size_t o, int n, int n1) {
+        const int n2 = n / n1;
+        auto one = [&](size_t i, long long e) {
+            const double a = 2.0 * M_PI * (double)(e % n) / (double)n, c = std::cos(a), sn = -std::sin(a);
+            if (mixed) { const float v[2] = {(float)c, (float)sn}; put(o + 8 * i, v, 8); }
+            else { const double v[2] = {c, sn}; put(o + 16 * i, v, 16); }
+        };
+        for (int q = 0; q < n1; ++q)
+            for (int c = 0; c < n2; ++c) one((size_t)q * n2 + c, (long long)q * c);
+        for (int p = 0; p < n2; ++p)
+            for (int q1 = 0; q1 < n1; ++q1) one((size_t)n + (size_t)p * n1 + q1, (long long)p * q1);
     };
-    tw(o_twx, d.nx);
-    tw(o_twy, d.ny);
+    tw(o_twx, d.nx, d.nx1);
+    tw(o_twy, d.ny, d.ny1);
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // pageable source: the copy is staged before cudaMemcpyAsync returns
