@@ -44,10 +44,10 @@ BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of each
 # kernel from one ncu capture (512x512x128 mixed, see profiles/), valid while the
 # kernel sources hash to SOURCES_SHA256; otherwise the roofline's traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.67, "x_forward_residual": 15.27, "correct": 64.69,
-                          "yz_forward": 8.42, "yz_backward": 8.43, "x_inverse_store": 6.57,
-                          "x_inverse_accumulate": 6.58}
-NCU_SOURCES_SHA256 = "106ce90aa4a73e759abd6ee307a02e02ee1f4c513c334e89dbf646147aebe65a"
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.69, "x_forward_residual": 15.23, "correct": 64.76,
+                          "yz_forward": 8.43, "yz_backward": 8.41, "x_inverse_store": 6.56,
+                          "x_inverse_accumulate": 6.56}
+NCU_SOURCES_SHA256 = "eda42e58ef5a419fb1878876d09c65a4e4b8a80acf08f176ab09ab30af4440f9"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_common.cuh", "ibf_device.cuh", "ibf_internal.h")
 
 
