@@ -196,6 +196,67 @@ def time_steps(plan, ins, outs, K, W, ws, flush=None):
     return max_over_ranks(ms, ws), prof
 
 
+# Factored implicit viscous solve (ibf_viscous_solve): algorithmic bytes per cell and
+# component of each launch (mixed path; fp64 path in brackets): x-FFT of the field 8 in +
+# 4 spectrum (8 + 8), y transforms with the factors 4 + 4 (8 + 8), inverse x-FFT 4 + 4
+# (8 + 8), z Thomas: read and write the forward sweep, read it back, write fp64 out 4+4+4+8
+# (8+8+8+8).
+VISC_BYTES = {"viscous_x_forward": (12.0, 16.0), "viscous_y": (8.0, 16.0), "viscous_x_inverse": (8.0, 16.0),
+              "viscous_z": (20.0, 32.0)}
+VISC_BETA = 1e-4  # beta = alpha dt / (2 Re); beta / dx^2 = 2.7 on the 1024^2 planes: strongly coupled lines
+
+
+def measure_viscous(plan, ins, outs, K, W, ws, mixed, cells, hbm_peak):
+    """W warm-up then K timed viscous solves of the three components (CUDA events on the
+    current stream); per-kernel profile, and the roofline of the dominant kernel."""
+    import torch
+    st = torch.cuda.current_stream()
+    outs = outs[:3]
+    for _ in range(W):
+        plan.viscous_solve_into([ins], [outs], VISC_BETA)
+    plan.profile(True)
+    plan.profile_read(reset=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(K):
+        plan.viscous_solve_into([ins], [outs], VISC_BETA)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
+    prof = plan.profile_read(reset=True)
+    plan.profile(False)
+    col = 0 if mixed else 1
+    kernels = {k: {"launches": c, "ms_per_launch": t / c,
+                   "gbs_algorithmic": VISC_BYTES[k][col] * cells / (t / c * 1e-3) / 1e9 if k in VISC_BYTES else None}
+               for k, (c, t) in prof.items()}
+    dname, (dc, dt_) = max(((k, v) for k, v in prof.items() if k in VISC_BYTES), key=lambda kv: kv[1][1])
+    achieved = VISC_BYTES[dname][col] * cells / (dt_ / dc * 1e-3) / 1e9
+    total_b = 3 * sum(b[col] for b in VISC_BYTES.values())
+    return {"ms_per_solve": ms, "value": ws * cells / (ms * 1e-3), "unit": "cells/s (three components)",
+            "bytes_per_cell_model": total_b, "hbm_frac": total_b * cells / (ms * 1e-3) / 1e9 / hbm_peak,
+            "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "bytes_per_cell": VISC_BYTES[dname][col]},
+            "kernels": kernels, "gpu_launches": int(sum(c for c, _ in prof.values()))}
+
+
+def viscous_oracle_sample(nx, ny, nz_sample):
+    """The viscous-solve oracle (oracle/viscous.py) timed on the host on nx x ny x nz_sample."""
+    import numpy as np
+    from oracle import oracle as O
+    from oracle import viscous as V
+    from paper_2609_19130_gb300 import synth
+    zf = O.zfaces_tanh(nz_sample, LZ, BETA)
+    u, v, w = synth.uniform_velocity_np(SEED, nx, ny, nz_sample)
+    t0 = time.perf_counter()
+    V.viscous_solve(nx, ny, nz_sample, LX, LY, zf, u, v, w, VISC_BETA)
+    sec = time.perf_counter() - t0
+    return {"value": nx * ny * nz_sample / sec, "unit": "cells/s (three components)", "cores": 1, "kind": "oracle",
+            "sample": f"fp64 numpy oracle (Thomas + Sherman-Morrison per line) on {nx}x{ny}x{nz_sample}, {sec:.1f} s"}
+
+
 def workload_config(nx, ny, nz, refine):
     return {"workload": f"{nx}x{ny}x{nz} staggered projection, periodic x,y (2pi), walls z in [0,2], "
                         f"tanh beta {BETA}; velocity = k^-5/3 Fourier modes + U[-0.01,0.01] noise (seed {SEED}); "
@@ -341,6 +402,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-viscous", action="store_true", help="skip the viscous-solve measurement")
     ap.add_argument("--autotune", type=int, default=0, help="1: plan-time autotuning of the launch shapes")
     ap.add_argument("--tuning", default="", help="JSON dict of ibf_tuning fields forced for the mixed plan")
     ap.add_argument("--batch64", action="store_true", help="time the 64-grid batched workload instead")
@@ -508,6 +570,19 @@ def main():
                        "pipelined": "upload of step i+1 and download of step i overlap step i's projection"}
         line["gpu_launches"] += int(round(launches_per_step * ke))
         del dev_sets, h_in, h_out
+
+    # the factored implicit viscous solve on the same workload and plans (separate object:
+    # not part of the projection's step)
+    if not args.no_viscous:
+        visc = {"beta": VISC_BETA,
+                "workload": f"{nx}x{ny}x{nz}: (I - beta Lz)^-1 (I - beta Ly)^-1 (I - beta Lx)^-1 of u, v, w "
+                            f"(the same fields as right-hand sides)"}
+        for prec, r in res.items():
+            visc["mixed" if prec == MIXED else "fp64"] = measure_viscous(
+                r["plan"], ins, outs, args.steps, args.warmup, ws, prec == MIXED, cells, hbm_peak)
+        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+            visc["cpu_oracle"] = viscous_oracle_sample(nx, ny, min(8, nz))
+        line["viscous_solve"] = visc
 
     for r in res.values():
         r["plan"].close()

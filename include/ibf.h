@@ -170,6 +170,32 @@ ibf_status ibf_project(ibf_plan *plan, const ibf_fields *in, const ibf_fields *o
 ibf_status ibf_project_backward(ibf_plan *plan, const ibf_fields *grad_out, const ibf_fields *grad_in,
                                 double dt, double alpha, void *stream);
 
+/* Factored implicit viscous solve (Section "Fluid Mechanics", Eq. nstime_discr with the
+ * viscous terms advanced by Crank-Nicolson; Section "Fluid domain", provisional-step
+ * paragraph: one tridiagonal solve per direction, Sherman-Morrison on the periodic
+ * lines), for each velocity component c = u, v, w of every grid of the plan:
+ *     out[g].c = (I - beta Lz)^-1 (I - beta Ly)^-1 (I - beta Lx)^-1 in[g].c,
+ *     beta = alpha dt / (2 Re) >= 0,
+ * with Lx, Ly the periodic second differences (spacing lx/nx, ly/ny; u on x-faces and
+ * v on y-faces are periodic like the cells) and Lz the second difference of the
+ * component's own z grid: for u and v the cell centres, no-slip walls at both z ends
+ * (mirror ghost -f at distance hz from the first and last centre); for w the interior
+ * faces 1..nz-1, whose wall faces 0 and nz are written as zero (in[g].w there is
+ * ignored).  The x and y inverses are exact inverses of the periodic operators (taken
+ * in the Fourier space of the projection's transforms); the z systems are solved by
+ * Thomas' algorithm with pivots formed in fp64 on the device (again whenever beta
+ * differs from the previous call's on this plan, and in every stream capture).
+ * in / out: ngrids ibf_fields of DEVICE fp64 velocity arrays in the projection's
+ * layouts (p and q ignored); out[g].c may alias in[g].c of the same component.
+ * Precision: the plan's.  IBF_FP64 computes in fp64; IBF_MIXED runs the transforms
+ * and the z sweeps in fp32 (fp64 input and output; relative error about 1e-6 of the
+ * largest output value).  Uses the plan's workspace: same stream and capture rules as
+ * ibf_project (no allocation, no host synchronisation).
+ * Errors: INVALID_ARG (null plan or arrays, beta negative or not finite),
+ * UNSUPPORTED_BC (a grid with a wall-bounded x or y), UNSUPPORTED_SIZE, CUDA. */
+ibf_status ibf_viscous_solve(ibf_plan *plan, const ibf_fields *in, const ibf_fields *out, double beta,
+                             void *stream);
+
 /* Launch shape of one grid, chosen by ibf_projection_plan (defaults or, with
  * opts->autotune, the fastest candidate timed on this device), or forced by the
  * caller through ibf_projection_plan_tuned.  Every field <= 0 means "default".

@@ -161,6 +161,35 @@ class Plan:
         s = N.lib().ibf_project_backward(self._h, fo, fi, float(dt), float(alpha), _stream_handle(stream))
         N.check(s, "ibf_project_backward")
 
+    def viscous_solve_into(self, ins, outs, beta, stream=None):
+        """Factored implicit viscous solve (ibf_viscous_solve): ins / outs per grid
+        (u, v, w) CUDA float64 tensors in the velocity layouts; outs may alias ins."""
+        n = len(self.grids)
+        fin = (N.ibf_fields * n)()
+        fout = (N.ibf_fields * n)()
+        for g in range(n):
+            u, v, w = ins[g][:3]
+            uo, vo, wo = outs[g][:3]
+            fin[g] = N.ibf_fields(u.data_ptr(), v.data_ptr(), w.data_ptr(), None)
+            fout[g] = N.ibf_fields(uo.data_ptr(), vo.data_ptr(), wo.data_ptr(), None)
+        s = N.lib().ibf_viscous_solve(self._h, fin, fout, float(beta), _stream_handle(stream))
+        N.check(s, "ibf_viscous_solve")
+
+    def viscous_solve(self, fields, beta, out=None, stream=None):
+        """(I - beta Lz)^-1 (I - beta Ly)^-1 (I - beta Lx)^-1 of each component of each
+        grid; fields: per grid (u, v, w).  Returns per grid (u, v, w), new tensors unless
+        `out` is given."""
+        import torch
+        if len(fields) != len(self.grids):
+            raise ValueError("one (u, v, w) per grid")
+        outs = []
+        for g, (grid, f) in enumerate(zip(self.grids, fields)):
+            for t, sh, nm in zip(f[:3], grid.shapes, ("u", "v", "w")):
+                _check_field(t, sh, nm)
+            outs.append(out[g] if out is not None else tuple(torch.empty_like(t) for t in f[:3]))
+        self.viscous_solve_into(fields, outs, beta, stream=stream)
+        return outs
+
     # ------------------------------------------------------------ conveniences
     def project(self, u, v, w, dt, alpha=1.0, out=None, stats=False, stream=None, p=None, q=None):
         """Single-grid convenience: returns (u, v, w, p) (new tensors unless `out` is given);

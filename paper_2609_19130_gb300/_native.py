@@ -30,7 +30,7 @@ IBF_MAX_GRIDS = 4096
 EXPORTS = ("ibf_projection_plan", "ibf_project", "ibf_project_backward", "ibf_plan_sync_status",
            "ibf_plan_destroy", "ibf_status_string", "ibf_last_error", "ibf_plan_get_info",
            "ibf_profile_enable", "ibf_profile_read", "ibf_profile_reset", "ibf_project_noalloc",
-           "ibf_projection_plan_tuned", "ibf_plan_get_tuning")
+           "ibf_projection_plan_tuned", "ibf_plan_get_tuning", "ibf_viscous_solve")
 
 
 class ibf_grid(C.Structure):
@@ -93,6 +93,8 @@ def lib():
         L.ibf_project_backward.argtypes = [vp, C.POINTER(ibf_fields), C.POINTER(ibf_fields), C.c_double,
                                            C.c_double, vp]
         L.ibf_project_backward.restype = C.c_int
+        L.ibf_viscous_solve.argtypes = [vp, C.POINTER(ibf_fields), C.POINTER(ibf_fields), C.c_double, vp]
+        L.ibf_viscous_solve.restype = C.c_int
         L.ibf_plan_sync_status.argtypes = [vp]
         L.ibf_plan_sync_status.restype = C.c_int
         L.ibf_plan_destroy.argtypes = [vp]

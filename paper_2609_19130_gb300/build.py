@@ -1,4 +1,4 @@
-"""Build libibf.so (sm_103a) in-tree with nvcc: two translation units compiled in parallel."""
+"""Build libibf.so (sm_103a) in-tree with nvcc: the translation units compiled in parallel."""
 import os
 import subprocess
 import sys
@@ -12,8 +12,8 @@ ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["ibf_kernels.cu", "ibf_yz.cu", "ibf_capi.cpp", "ibf_noalloc.cu"]
-HEADERS = ["ibf_device.cuh", "ibf_common.cuh", "ibf_internal.h", "tw96.inc"]
+SOURCES = ["ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_capi.cpp", "ibf_noalloc.cu"]
+HEADERS = ["ibf_device.cuh", "ibf_common.cuh", "ibf_internal.h", "ibf_viscous.h", "tw96.inc"]
 
 
 def _nvcc():

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "ibf_internal.h"
+#include "ibf_viscous.h"
 
 using namespace ibf;
 
@@ -76,6 +77,15 @@ struct ibf_plan {
     std::vector<void *> allocs;
     Work work{};
     size_t xsmem = 0, yzsmem = 0, slabsmem = 0, yfftsmem = 0;
+    // viscous solve: pivots of (I - beta Lz) per grid (6 (nz+1) entries at 6 z_off) and the
+    // shared memory of its y kernel
+    double *helm = nullptr, *fxy = nullptr;
+    float *helmf = nullptr, *fxyf = nullptr;
+    long long *fxy_off_dev = nullptr;   // per grid: offset of its x / y factors (nxh + ny entries)
+    std::vector<long long> fxy_off;
+    size_t helmsmem = 0, smemcap = 0;
+    bool helm_valid = false;            // the tables hold the factors of helm_beta
+    double helm_beta = 0.0;
     int nxblk = 0, nyzblk = 0, nstrblk = 0, nslabblk = 0, nyfftblk = 0, nsweepblk = 0, maxnz = 0;
     long long ws_bytes = 0;
     long long total_cells = 0;
@@ -392,11 +402,14 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
             maxyz = std::max(maxyz, n.yz);
             maxslab = std::max(maxslab, n.slab);
             maxyfft = std::max(maxyfft, n.yfft);
+            const size_t csz = mixed ? 8 : 16;
+            pl->helmsmem = std::max(pl->helmsmem, (size_t)t.mb * (size_t)(t.y_n1 * (d.ny2 + 1) + 1) * csz);
         }
         pl->maxnz = std::max(pl->maxnz, d.nz);
         pl->total_cells += (long long)d.nx * d.ny * d.nz;
     }
     const size_t cap = smem_cap(prop);
+    pl->smemcap = cap;
     if (maxx > cap || maxyz > cap || maxslab > cap || maxyfft > cap || (size_t)10 * (pl->maxnz + 1) * 8 > cap)
         return IBF_ERR_UNSUPPORTED_SIZE;
     str_start[ngrids] = strblk;
@@ -489,6 +502,20 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     IBF_TRY(dalloc(pl, &w.z.czf, sizeof(float) * nzt));
     IBF_TRY(dalloc(pl, &w.z.rhz_df, sizeof(float2) * nzt));
     IBF_TRY(dalloc(pl, &w.z.rgzf_df, sizeof(float2) * nzt));
+    IBF_TRY(dalloc(pl, &pl->helm, sizeof(double) * 6 * (size_t)nzt));
+    IBF_TRY(dalloc(pl, &pl->helmf, sizeof(float) * 6 * (size_t)nzt));
+    {
+        long long nf = 0;
+        pl->fxy_off.resize(ngrids);
+        for (int g = 0; g < ngrids; ++g) {
+            pl->fxy_off[g] = nf;
+            nf += pl->grids[g].d.nxh + pl->grids[g].d.ny;
+        }
+        IBF_TRY(dalloc(pl, &pl->fxy, sizeof(double) * (size_t)nf));
+        IBF_TRY(dalloc(pl, &pl->fxyf, sizeof(float) * (size_t)nf));
+        IBF_TRY(dalloc(pl, &pl->fxy_off_dev, sizeof(long long) * (size_t)ngrids));
+        IBF_TRY(upload(pl->fxy_off.data(), pl->fxy_off_dev, sizeof(long long) * (size_t)ngrids));
+    }
     IBF_TRY(dalloc(pl, &w.spec, csz * (size_t)spec));
     IBF_TRY(dalloc(pl, &w.tab, rsz * (size_t)spec));
     void *twx, *twy;
@@ -553,6 +580,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
 
     e = set_smem_limits(mixed);
+    if (e == cudaSuccess) e = set_smem_limits_visc(mixed);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     e = launch_build_table(mixed, w, pl->nyzblk, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "pivot table kernel");
@@ -964,6 +992,78 @@ ibf_status ibf_project_backward(ibf_plan *plan, const ibf_fields *grad_out, cons
     cudaError_t e = cudaSetDevice(plan->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     return run(plan, grad_out, grad_in, dt, alpha, nullptr, static_cast<cudaStream_t>(stream), 1);
+}
+
+ibf_status ibf_viscous_solve(ibf_plan *plan, const ibf_fields *in, const ibf_fields *out, double beta,
+                             void *stream) {
+    if (!plan || !fields_ok(in, plan->ngrids, false) || !fields_ok(out, plan->ngrids, false)) return IBF_ERR_INVALID_ARG;
+    if (!(beta >= 0) || !std::isfinite(beta)) return IBF_ERR_INVALID_ARG;
+    for (int g = 0; g < plan->ngrids; ++g)
+        if (plan->grids[g].d.wall_x || plan->grids[g].d.wall_y) {
+            g_last_error = "viscous solve: x and y must be periodic";
+            return IBF_ERR_UNSUPPORTED_BC;
+        }
+    if (plan->helmsmem > plan->smemcap) {
+        g_last_error = "viscous solve: the y transform of a column block does not fit in shared memory";
+        return IBF_ERR_UNSUPPORTED_SIZE;
+    }
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    ibf_plan *pl = plan;
+    Ctx c{pl, static_cast<cudaStream_t>(stream)};
+    const Work &w = pl->work;
+    const int mixed = pl->mixed;
+    // the pivots and factors depend on beta only: rebuilt when it changes, and always
+    // inside a stream capture (the graph then carries its own tables)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c.st, &cap) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaStreamIsCapturing");
+    if (!pl->helm_valid || pl->helm_beta != beta || cap != cudaStreamCaptureStatusNone) {
+        IBF_TRY(timed(c, "helm_table", [&]() {
+            return launch_helm_table(w, pl->ngrids, beta, pl->helm, pl->helmf, pl->fxy_off_dev, pl->fxy, pl->fxyf,
+                                     c.st);
+        }));
+        pl->helm_valid = true;
+        pl->helm_beta = beta;
+    }
+    // one velocity component at a time: x-FFT of the field, the x and y factors between
+    // the y transforms, inverse x-FFT into the per-cell workspace, Thomas along z
+    for (int comp = 0; comp < 3; ++comp) {
+        std::vector<ibf_fields> cin(pl->ngrids);
+        for (int g = 0; g < pl->ngrids; ++g) {
+            cin[g] = ibf_fields{};
+            cin[g].u = const_cast<double *>(comp == 0 ? in[g].u : (comp == 1 ? in[g].v : in[g].w));
+            cin[g].v = cin[g].w = cin[g].u;
+        }
+        for (int g0 = 0; g0 < pl->ngrids; g0 += kGridsPerLaunch) {
+            const int g1 = std::min(pl->ngrids, g0 + kGridsPerLaunch);
+            UserPtrs p;
+            fill_ptrs(pl, p, g0, g1, cin.data(), nullptr);
+            p.zshift = comp == 2;
+            const int nb = chunk_blocks(pl, g0, g1);
+            IBF_TRY(timed(c, "viscous_x_forward", [&]() {
+                return launch_xfwd(mixed, XM_COPY, w, p, 1, 0, nb, 1.0, 1.0, pl->xsmem, c.st);
+            }));
+        }
+        for (int g = 0; g < pl->ngrids; ++g) {
+            const GridDev &d = pl->grids[g].d;
+            IBF_TRY(timed(c, "viscous_y", [&]() {
+                return launch_yhelm(mixed, w, g, d.nz * d.ncb, pl->fxy + pl->fxy_off[g], pl->fxyf + pl->fxy_off[g],
+                                    pl->helmsmem, c.st);
+            }));
+        }
+        IBF_TRY(for_chunks(c, "viscous_x_inverse", cin.data(), nullptr, [&](const UserPtrs &p, int nb) {
+            return launch_xinv(mixed, IM_STORE, w, p, 1, 0, nb, pl->xsmem, c.st);
+        }));
+        for (int g = 0; g < pl->ngrids; ++g) {
+            const GridDev &d = pl->grids[g].d;
+            double *o = comp == 0 ? out[g].u : (comp == 1 ? out[g].v : out[g].w);
+            IBF_TRY(timed(c, "viscous_z", [&]() {
+                return launch_zhelm(mixed, w, g, (long long)d.nx * d.ny, comp == 2, pl->helm, pl->helmf, o, c.st);
+            }));
+        }
+    }
+    pl->last_stream = c.st;
+    return IBF_OK;
 }
 
 ibf_status ibf_plan_sync_status(ibf_plan *plan) {

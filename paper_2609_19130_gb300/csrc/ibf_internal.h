@@ -97,11 +97,14 @@ struct UserPtrs {
     const double *in_q[kGridsPerLaunch];  // mass sources of Eq. (elliptic) (may be null)
     int g0, g1;                // grids [g0, g1) of this launch
     int blk0;                  // first block index (x-kernel numbering) of grid g0
+    int zshift;                // XM_COPY: plane k of the transform reads plane k + zshift of in_u
+                               // (1: interior z-faces of w; the last plane is then zero)
 };
 
 // x-forward modes: right-hand side of the first solve, refinement residual (phi a
 // float-float pair), adjoint source, refinement residual of the first sweep (phi plain fp32)
-enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2, XM_RESID0 = 3, XM_DIVQ = 4 /* XM_DIV with a mass source q */ };
+enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2, XM_RESID0 = 3, XM_DIVQ = 4 /* XM_DIV with a mass source q */,
+             XM_COPY = 5 /* the field in_u itself (viscous solve): no stencil, no plane sums */ };
 enum InvMode { IM_STORE = 0, IM_ACCUM = 1 };
 
 // Launchers (ibf_kernels.cu).  T = 0: fp64 path, 1: mixed path.

@@ -107,7 +107,26 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
         const bool own_up = (lane == 31) || (ii + 1 == nx);
         const bool own_dn = (lane == 0) || (ii == 0);
         const int spos = pos_nat(wall_x ? dct_perm(ii, nx) : ii, fN2);
-        if (DIVL || MODE == XM_ADJ) {
+        if constexpr (MODE == XM_COPY) {
+            // the field itself, one row after the other (plane k + zshift; zero past the
+            // last interior face of w)
+            const bool live = !(p.zshift && k == nz - 1);
+            const double *src = p.in_u[gi] + (ptrdiff_t)(k + p.zshift) * plane;
+            for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
+                double v[kRowGroup];
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+                    v[q] = (act && live && jl < sm.r1 && j < ny) ? __ldg(src + (ptrdiff_t)j * nx + i) : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    const int jl = jg + q;
+                    if (jl >= sm.r1) break;
+                    if (act) *(reinterpret_cast<T *>(buf + (jl >> 1) * sstride + spos) + (jl & 1)) = (T)v[q] * scale;
+                }
+            }
+        } else if (DIVL || MODE == XM_ADJ) {
             // wall-bounded x: u rows hold nx+1 faces; wall-bounded y: v planes hold ny+1 rows
             const double *u = p.in_u[gi] + (ptrdiff_t)k * ny * nxu;
             const double *vv = p.in_v[gi] + (ptrdiff_t)k * (W ? G.nyv : ny) * nx, *ww = p.in_w[gi] + pbase;
@@ -360,7 +379,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     if (DIVL || MODE == XM_ADJ) {
         V tot = Red<A>::sum(acc, red);
         if (threadIdx.x == 0) w.partial[G.part_off + k * nrb + rb] = A::store(tot);
-    } else {
+    } else if (MODE != XM_COPY) {
         V totp = Red<A>::sum(acc_phi, red);
         if (threadIdx.x == 0) w.partial_phi[G.part_off + k * nrb + rb] = A::store(totp);
     }
@@ -775,7 +794,10 @@ cudaError_t launch_xfwd_w(int mixed, int mode, const Work &w, const UserPtrs &p,
             k_xfwd<float, DFArith, XM_RESID0, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else if (mode == XM_RESID)
             k_xfwd<float, DFArith, XM_RESID, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else
+        else if (mode == XM_COPY) {
+            if constexpr (W) return cudaErrorInvalidValue;  // periodic x and y only
+            else k_xfwd<float, DFArith, XM_COPY, false><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        } else
             k_xfwd<float, DFArith, XM_ADJ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
     } else {
         if (mode == XM_DIV)
@@ -784,7 +806,10 @@ cudaError_t launch_xfwd_w(int mixed, int mode, const Work &w, const UserPtrs &p,
             k_xfwd<double, F64Arith, XM_DIVQ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
         else if (mode == XM_ADJ)
             k_xfwd<double, F64Arith, XM_ADJ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else
+        else if (mode == XM_COPY) {
+            if constexpr (W) return cudaErrorInvalidValue;
+            else k_xfwd<double, F64Arith, XM_COPY, false><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+        } else
             return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -897,6 +922,8 @@ cudaError_t set_smem_limits(int mixed) {
     };
     set_all(std::false_type{});
     set_all(std::true_type{});
+    if (mixed) set((const void *)k_xfwd<float, DFArith, XM_COPY, false>);
+    else set((const void *)k_xfwd<double, F64Arith, XM_COPY, false>);
     if (e == cudaSuccess) e = set_smem_limits_yz(mixed);
     return e;
 }
