@@ -403,7 +403,8 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
             maxslab = std::max(maxslab, n.slab);
             maxyfft = std::max(maxyfft, n.yfft);
             const size_t csz = mixed ? 8 : 16;
-            pl->helmsmem = std::max(pl->helmsmem, (size_t)t.mb * (size_t)(t.y_n1 * (d.ny2 + 1) + 1) * csz);
+            pl->helmsmem = std::max(pl->helmsmem, (size_t)(yhelm_group(t.mb) * t.mb) *
+                                                      (size_t)(t.y_n1 * (d.ny2 + 1) + 1) * csz);
         }
         pl->maxnz = std::max(pl->maxnz, d.nz);
         pl->total_cells += (long long)d.nx * d.ny * d.nz;
@@ -1047,8 +1048,9 @@ ibf_status ibf_viscous_solve(ibf_plan *plan, const ibf_fields *in, const ibf_fie
         for (int g = 0; g < pl->ngrids; ++g) {
             const GridDev &d = pl->grids[g].d;
             IBF_TRY(timed(c, "viscous_y", [&]() {
-                return launch_yhelm(mixed, w, g, d.nz * d.ncb, pl->fxy + pl->fxy_off[g], pl->fxyf + pl->fxy_off[g],
-                                    pl->helmsmem, c.st);
+                const int gb = yhelm_group(d.mb);
+                return launch_yhelm(mixed, w, g, d.nz * ((d.ncb + gb - 1) / gb), gb, pl->fxy + pl->fxy_off[g],
+                                    pl->fxyf + pl->fxy_off[g], pl->helmsmem, c.st);
             }));
         }
         IBF_TRY(for_chunks(c, "viscous_x_inverse", cin.data(), nullptr, [&](const UserPtrs &p, int nb) {

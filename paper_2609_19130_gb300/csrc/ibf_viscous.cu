@@ -88,41 +88,51 @@ __global__ void k_helm_table(Work w, double beta, double *tab, float *tabf, cons
 }
 
 // y-FFT, multiplication by fx_m fy_n with fx_m = 1/(1 + beta (4/dx^2) sin^2(pi m/nx))
-// and fy_n likewise (tables of k_helm_table), inverse y-FFT: one (plane, column block) of
-// grid g's x-spectrum, in place (row order in and out).  The x-FFT scaled by 1/(nx ny), so
-// the unnormalised inverse transforms return the field.
+// and fy_n likewise (tables of k_helm_table), inverse y-FFT: gb consecutive column blocks
+// (cb0 .. cb0 + gb - 1, each mb x-modes) of one plane of grid g's x-spectrum, in place
+// (row order in and out), as one batch of gb mb sequences so that the FFT passes have
+// work for every warp when the blocks are narrow.  The x-FFT scaled by 1/(nx ny), so the
+// unnormalised inverse transforms return the field.
 template <typename T>
-__global__ void __launch_bounds__(kYZThreads) k_yhelm(Work w, int g, const T *fxy) {
+__global__ void __launch_bounds__(kYZThreads) k_yhelm(Work w, int g, int gb, const T *fxy) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const GridDev &G = w.grids[g];
-    const int ncb = G.ncb, k = blockIdx.x / ncb, cb = blockIdx.x - k * ncb;
+    const int ncb = G.ncb, ngrp = (ncb + gb - 1) / gb;
+    const int k = blockIdx.x / ngrp, cb0 = (blockIdx.x - k * ngrp) * gb;
     const int ny = G.ny, mb = G.mb, nxh = G.nxh;
     const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
     const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
-    const int nslot = ny * mb, nvalid = min(mb, nxh - cb * mb);
+    const int nslot = ny * mb;
+    const int nb = min(gb, ncb - cb0);                 // column blocks of this group
+    const int nmode = min(nb * mb, nxh - cb0 * mb);    // valid x-modes of the group
     const cx<T> *twy = reinterpret_cast<const cx<T> *>(w.twy) + G.twy_off;
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
-    cx<T> *pl = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + ((size_t)k * ncb + cb) * nslot;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int t = tid; t < nslot; t += nthr) {
-        const int r = (int)fdiv((unsigned)t, fmb), mm = t - r * mb;
-        buf[mm * sstride + pos_nat(r, fN2)] = (mm < nvalid) ? pl[t] : cx<T>{(T)0, (T)0};
+    cx<T> *pl = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + ((size_t)k * ncb + cb0) * nslot;
+    const int tid = threadIdx.x, nthr = blockDim.x, ntot = gb * nslot;
+    // element t of the group: column block q = t / nslot, slot t - q nslot = r mb + mm;
+    // sequence s = q mb + mm (x-mode cb0 mb + s)
+    for (int t = tid; t < ntot; t += nthr) {
+        const int q = t / nslot, ts = t - q * nslot;
+        const int r = (int)fdiv((unsigned)ts, fmb), sq = q * mb + (ts - r * mb);
+        buf[sq * sstride + pos_nat(r, fN2)] = (sq < nmode) ? pl[t] : cx<T>{(T)0, (T)0};
     }
     __syncthreads();
-    fft_batch<T, -1>(buf, mb, sstride, N1, N2, fN1, fN2, twy);
-    const T *fx = fxy, *fy = fxy + nxh;
-    for (int t = tid; t < nslot; t += nthr) {
-        const int n = (int)fdiv((unsigned)t, fmb), mm = t - n * mb;  // y-mode n of x-mode cb mb + mm
-        if (mm >= nvalid) continue;
-        const T f = fx[cb * mb + mm] * fy[n];
-        cx<T> &v = buf[mm * sstride + pos_tr(n, N1, N2, fN1)];
+    fft_batch<T, -1>(buf, gb * mb, sstride, N1, N2, fN1, fN2, twy);
+    const T *fx = fxy + cb0 * mb, *fy = fxy + nxh;
+    for (int t = tid; t < ntot; t += nthr) {
+        const int q = t / nslot, ts = t - q * nslot;
+        const int n = (int)fdiv((unsigned)ts, fmb), sq = q * mb + (ts - n * mb);  // y-mode n of sequence sq
+        if (sq >= nmode) continue;
+        const T f = fx[sq] * fy[n];
+        cx<T> &v = buf[sq * sstride + pos_tr(n, N1, N2, fN1)];
         v = {v.x * f, v.y * f};
     }
     __syncthreads();
-    fft_batch<T, +1>(buf, mb, sstride, N1, N2, fN1, fN2, twy);
-    for (int t = tid; t < nslot; t += nthr) {
-        const int r = (int)fdiv((unsigned)t, fmb), mm = t - r * mb;
-        if (mm < nvalid) pl[t] = buf[mm * sstride + pos_nat(r, fN2)];
+    fft_batch<T, +1>(buf, gb * mb, sstride, N1, N2, fN1, fN2, twy);
+    for (int t = tid; t < ntot; t += nthr) {
+        const int q = t / nslot, ts = t - q * nslot;
+        const int r = (int)fdiv((unsigned)ts, fmb), sq = q * mb + (ts - r * mb);
+        if (sq < nmode) pl[t] = buf[sq * sstride + pos_nat(r, fN2)];
     }
 }
 
@@ -177,11 +187,11 @@ cudaError_t launch_helm_table(const Work &w, int ngrids, double beta, double *ta
     return cudaGetLastError();
 }
 
-cudaError_t launch_yhelm(int mixed, const Work &w, int g, int nblk, const double *fxy, const float *fxyf,
+cudaError_t launch_yhelm(int mixed, const Work &w, int g, int nblk, int gb, const double *fxy, const float *fxyf,
                          size_t smem, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
-    if (mixed) k_yhelm<float><<<nblk, kYZThreads, smem, st>>>(w, g, fxyf);
-    else k_yhelm<double><<<nblk, kYZThreads, smem, st>>>(w, g, fxy);
+    if (mixed) k_yhelm<float><<<nblk, kYZThreads, smem, st>>>(w, g, gb, fxyf);
+    else k_yhelm<double><<<nblk, kYZThreads, smem, st>>>(w, g, gb, fxy);
     return cudaGetLastError();
 }
 
