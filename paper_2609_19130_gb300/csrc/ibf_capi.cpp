@@ -396,6 +396,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         d.fmb = make_fdiv(d.mb);
         d.frows = make_fdiv(d.rows);
         d.fnpair = make_fdiv(d.rows / 2);
+        d.fnpair2 = make_fdiv(std::max(1, d.rows / 4));
         {
             const SmemNeed n = smem_need(H.g, mixed, t);
             maxx = std::max(maxx, n.x);
@@ -476,6 +477,9 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     w.ngrids = ngrids;
     w.walls = 0;
     for (int g = 0; g < ngrids; ++g) w.walls |= pl->grids[g].d.wall_x | pl->grids[g].d.wall_y;
+    w.xinv_split = mixed ? 1 : 0;
+    for (int g = 0; g < ngrids; ++g)
+        if (pl->grids[g].d.rows % 4 != 0) w.xinv_split = 0;
     GridDev *dgrids;
     IBF_TRY(dalloc(pl, &dgrids, sizeof(GridDev) * ngrids));
     w.grids = dgrids;

@@ -49,6 +49,7 @@ struct GridDev {
     double inv_nxy;            // 1 / (nx ny)
     double sum_hz;             // lz
     FDiv fnx, fnx1, fnx2, fny1, fny2, fmb, frows, fnpair, fnph;  // fnph: nx/2 + 1
+    FDiv fnpair2;              // rows / 4 (row pairs of the half-block CTAs of the inverse x-FFT)
 };
 
 // Per-level arrays (index z_off + k; nz+1 entries per grid, the last one only used where noted).
@@ -67,6 +68,7 @@ struct Work {
     const GridDev *grids;      // [ngrids]
     int ngrids;
     int walls;                 // some grid has a wall-bounded x or y (selects the kernels that handle it)
+    int xinv_split;            // mixed path, every grid's rows divisible by 4: half-block inverse x-FFT CTAs
     const int *xblk_start;     // prefix of x-kernel blocks over grids [ngrids+1]
     const int *yzblk_start;    // prefix of column blocks over all grids [ngrids+1] (pivot table)
     const int *ystr_start;     // prefix of column blocks over grids with streaming y/z kernels

@@ -442,24 +442,28 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
 // Inverse real FFT along x of a block of rows; STORE writes phi (fp64 path: fp64
 // array; mixed path: the hi array of the float-float phi), ACCUM adds the
 // refinement correction to the float-float phi.
-template <typename T, class A, int IMODE, bool W>
-__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
+// SPLIT = 2: two CTAs of kXThreads / 2 threads per row block, each transforming half
+// of its rows (every grid of the plan has rows divisible by 4): twice the CTAs per SM
+// at the same warp count, so that one CTA's FFT overlaps another's gather and store.
+template <typename T, class A, int IMODE, bool W, int SPLIT>
+__global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T) == 4 ? 2 : 1))
     k_xinv(Work w, UserPtrs p, int use_ws, int lo_valid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
-    const int b = blockIdx.x + p.blk0;
+    const int b = blockIdx.x / SPLIT + p.blk0;
+    const int half = SPLIT == 2 ? (int)(blockIdx.x & 1u) : 0;
     const int g = find_grid(w.xblk_start, w.ngrids, b);
     const GridDev &G = w.grids[g];
     const int lb = b - __ldg(w.xblk_start + g);
-    const int nrb = G.nrb, rows = G.rows;
+    const int nrb = G.nrb, rows = G.rows / SPLIT;
     const int k = lb / nrb, rb = lb - k * nrb;
-    const int j0 = rb * rows;
+    const int j0 = rb * G.rows + half * rows;
     const int nx = G.nx, ny = G.ny;
     // sequences one complex element further apart than their length, so that the
     // split / gather steps, which read the same position of several sequences, do not
     // fall into one shared-memory bank
     const int N1 = G.nx1, N2 = G.nx2, sstride = fft_seq_len(N1, N2) + 1;
-    const FDiv fN1 = G.fnx1, fN2 = G.fnx2, fmb = G.fmb, fnpair = G.fnpair, fnx = G.fnx;
+    const FDiv fN1 = G.fnx1, fN2 = G.fnx2, fmb = G.fmb, fnpair = SPLIT == 2 ? G.fnpair2 : G.fnpair, fnx = G.fnx;
     const int mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const cx<T> *spec = reinterpret_cast<const cx<T> *>(w.spec) + G.spec_off + (size_t)k * ncb * ny * mb;
     const cx<T> *twx = reinterpret_cast<const cx<T> *>(w.twx) + G.twx_off;
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const int gi = g - p.g0;
     const ptrdiff_t plane = (ptrdiff_t)nx * ny;
     const ptrdiff_t base = (ptrdiff_t)k * plane + (ptrdiff_t)j0 * nx;
-    const int ncell = min(rows, ny - j0) * nx;
+    const int ncell = max(0, min(rows, ny - j0)) * nx;
     double *phi64 = nullptr;
     float *phh = nullptr, *phl = nullptr;
     if (sizeof(T) == 8) phi64 = (use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi]) + base;
@@ -825,13 +829,19 @@ cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, i
 template <bool W>
 cudaError_t launch_xinv_w(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
                           size_t smem, cudaStream_t st) {
-    if (mixed) {
+    if (mixed && w.xinv_split) {
+        const dim3 gr = grid1(2 * nblk);
         if (mode == IM_STORE)
-            k_xinv<float, DFArith, IM_STORE, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+            k_xinv<float, DFArith, IM_STORE, W, 2><<<gr, kXThreads / 2, smem / 2, st>>>(w, p, use_ws, lo_valid);
         else
-            k_xinv<float, DFArith, IM_ACCUM, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+            k_xinv<float, DFArith, IM_ACCUM, W, 2><<<gr, kXThreads / 2, smem / 2, st>>>(w, p, use_ws, lo_valid);
+    } else if (mixed) {
+        if (mode == IM_STORE)
+            k_xinv<float, DFArith, IM_STORE, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+        else
+            k_xinv<float, DFArith, IM_ACCUM, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
     } else {
-        k_xinv<double, F64Arith, IM_STORE, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+        k_xinv<double, F64Arith, IM_STORE, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
     }
     return cudaGetLastError();
 }
@@ -911,13 +921,15 @@ cudaError_t set_smem_limits(int mixed) {
             set((const void *)k_xfwd<float, DFArith, XM_RESID, W>);
             set((const void *)k_xfwd<float, DFArith, XM_RESID0, W>);
             set((const void *)k_xfwd<float, DFArith, XM_ADJ, W>);
-            set((const void *)k_xinv<float, DFArith, IM_STORE, W>);
-            set((const void *)k_xinv<float, DFArith, IM_ACCUM, W>);
+            set((const void *)k_xinv<float, DFArith, IM_STORE, W, 1>);
+            set((const void *)k_xinv<float, DFArith, IM_ACCUM, W, 1>);
+            set((const void *)k_xinv<float, DFArith, IM_STORE, W, 2>);
+            set((const void *)k_xinv<float, DFArith, IM_ACCUM, W, 2>);
         } else {
             set((const void *)k_xfwd<double, F64Arith, XM_DIV, W>);
             set((const void *)k_xfwd<double, F64Arith, XM_DIVQ, W>);
             set((const void *)k_xfwd<double, F64Arith, XM_ADJ, W>);
-            set((const void *)k_xinv<double, F64Arith, IM_STORE, W>);
+            set((const void *)k_xinv<double, F64Arith, IM_STORE, W, 1>);
         }
     };
     set_all(std::false_type{});

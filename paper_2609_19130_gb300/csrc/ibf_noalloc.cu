@@ -160,6 +160,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     d.fnph = fdiv_of(d.nx / 2 + 1);
     d.fny1 = fdiv_of(d.ny1); d.fny2 = fdiv_of(d.ny2);
     d.fmb = fdiv_of(d.mb); d.frows = fdiv_of(d.rows); d.fnpair = fdiv_of(d.rows / 2);
+    d.fnpair2 = fdiv_of(d.rows / 4 > 0 ? d.rows / 4 : 1);
     const size_t cells = (size_t)d.nx * d.ny * nz;
     const size_t nspec = (size_t)nz * d.ncb * d.ny * d.mb;
     const size_t xsmem = (size_t)(d.rows / 2) * (size_t)(d.nx1 * (d.nx2 + 1) + 1) * csz;
