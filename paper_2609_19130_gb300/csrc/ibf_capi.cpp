@@ -250,6 +250,7 @@ SmemNeed smem_need(const ibf_grid &g, int mixed, const ibf_tuning &t) {
         const size_t fwd = kYZStages * ((t.mb * sstr * csz + nslot * rsz + 15) & ~(size_t)15) + nslot * csz;
         const size_t bwd = kYZStages * ((nslot * (csz + rsz) + 15) & ~(size_t)15) + (t.mb * sstr + nslot) * csz;
         n.yz = std::max(fwd, bwd);
+        if (mixed && t.mb == 1 && g.bc_y != IBF_BC_NEUMANN) n.yz = std::max(n.yz, yz_pipe_smem(g.ny, (int)sstr));
     } else if (t.yz_kernel == 2) {
         n.slab = (((size_t)g.nz * t.mb * sstr * csz) + 15) & ~(size_t)15;
         if (t.tri > 1) n.slab += 3 * (size_t)g.nz * nslot * rsz;

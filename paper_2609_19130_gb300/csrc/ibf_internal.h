@@ -15,6 +15,17 @@ constexpr int kYZStages = 2;     // planes in flight per column block in the yz 
 // CTAs of the streaming y/z kernels resident per SM (registers: fp32 kernels are capped at
 // 128 registers per thread; the fp64 ones use about 255)
 constexpr int kYZResidentF32 = 4, kYZResidentF64 = 2;
+// Pipelined streaming y/z kernels (mixed path, one x-mode per column block, periodic y):
+// ring entries of FFT buffers (and pivot chunks) in shared memory
+constexpr int kPipeF = 3;  // forward: [FFT buffer | pivots] for the planes being copied, transformed, swept
+constexpr int kPipeB = 4;  // backward: FFT buffers being copied, swept, transformed, stored (pivots: 2)
+__host__ __device__ inline size_t pipe_align16(size_t b) { return (b + 15) & ~(size_t)15; }
+// shared memory of the pipelined kernels; sstr = padded FFT sequence length (complex)
+inline size_t yz_pipe_smem(int ny, int sstr) {
+    const size_t fwd = kPipeF * pipe_align16((size_t)sstr * 8 + (size_t)ny * 4) + (size_t)ny * 8;
+    const size_t bwd = kPipeB * pipe_align16((size_t)sstr * 8) + 2 * pipe_align16((size_t)ny * 4) + (size_t)ny * 8;
+    return fwd > bwd ? fwd : bwd;
+}
 constexpr int kSlabThreads = 256;  // resident-slab y/z kernel
 constexpr int kSweepThreads = 256; // split y/z path: Thomas sweeps, one thread per mode
 

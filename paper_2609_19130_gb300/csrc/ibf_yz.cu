@@ -58,6 +58,166 @@ __device__ __forceinline__ void dct_pre(cx<T> *buf, int nseq, int sstride, int N
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- pipelined forms
+// Mixed path, one x-mode per column block (mb = 1), periodic y.  A single sequence's
+// two-level FFT is 32 tasks per pass, so in the plain streaming kernels one warp
+// transforms each plane while the other three wait at the barriers.  Here warp 0 only
+// transforms and warps 1-3 run the Thomas sweep and the copies of neighbouring planes
+// in the same interval, one __syncthreads per plane:
+//   forward,  iteration it: warp 0 FFT of plane it;  warps 1-3 sweep plane it-1, copy plane it+1
+//   backward, iteration it: warp 0 inverse FFT of plane it-1;  warps 1-3 back-substitute
+//             plane it (in place in its FFT buffer), store plane it-2, copy plane it+1
+// (backward planes counted from the top).  Every slot is handled by the same warp-1-3
+// thread in the copies, the sweep and the store, so that thread alone reads what it
+// copied; what warp 0 transformed is read after the barrier that ends its iteration.
+// Shared memory (yz_pipe_smem): forward kPipeF x [FFT buffer | pivot chunk] + state;
+// backward kPipeB FFT buffers + 2 pivot chunks + state.
+constexpr int kPipeT = kYZThreads - 32;  // sweep / copy threads
+
+__device__ __forceinline__ void fft1_warp_fwd(cx<float> *buf, int sstride, int N1, int N2, const FDiv &fN1,
+                                              const FDiv &fN2, const cx<float> *tw, int lane) {
+    fft_col_pass<float, -1>(buf, 1, sstride, N1, N2, fN2, tw, lane, 32);
+    __syncwarp();
+    fft_row_pass<float, -1>(buf, 1, sstride, N1, N2, fN1, tw, lane, 32);
+    __syncwarp();
+}
+__device__ __forceinline__ void fft1_warp_inv(cx<float> *buf, int sstride, int N1, int N2, const FDiv &fN1,
+                                              const FDiv &fN2, const cx<float> *tw, int lane) {
+    fft_row_pass<float, +1>(buf, 1, sstride, N1, N2, fN1, tw, lane, 32);
+    __syncwarp();
+    fft_col_pass<float, +1>(buf, 1, sstride, N1, N2, fN2, tw, lane, 32);
+    __syncwarp();
+}
+
+__device__ void yzfwd_pipe(const Work &w, const GridDev &G, int cb, unsigned char *smem) {
+    const int ny = G.ny, nz = G.nz, ncb = G.ncb;
+    const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fny1, fN2 = G.fny2;
+    const size_t stage = pipe_align16((size_t)sstride * 8 + (size_t)ny * 4);
+    auto fb = [&](int i) { return reinterpret_cast<cx<float> *>(smem + (size_t)(i % kPipeF) * stage); };
+    auto tb = [&](int i) { return reinterpret_cast<float *>(smem + (size_t)(i % kPipeF) * stage + (size_t)sstride * 8); };
+    cx<float> *state = reinterpret_cast<cx<float> *>(smem + (size_t)kPipeF * stage);
+    const cx<float> *spec = reinterpret_cast<const cx<float> *>(w.spec) + G.spec_off;
+    cx<float> *specw = reinterpret_cast<cx<float> *>(w.spec) + G.spec_off;
+    const float *tab = reinterpret_cast<const float *>(w.tab) + G.tab_off;
+    const cx<float> *twy = reinterpret_cast<const cx<float> *>(w.twy) + G.twy_off;
+    const float *az = w.z.azf + G.z_off;
+    const int tid = threadIdx.x, tt = tid - 32;
+    const bool fw = tid < 32;
+    auto issue = [&](int k) {  // spectrum and pivots of plane k into ring entry k
+        if (k < nz) {
+            cx<float> *f = fb(k);
+            float *t = tb(k);
+            const cx<float> *src = spec + ((size_t)k * ncb + cb) * ny;
+            const float *tsrc = tab + ((size_t)k * ncb + cb) * ny;
+            for (int j = tt; j < ny; j += kPipeT) {
+                cp_async<8>(f + pos_nat(j, fN2), src + j);
+                cp_async<4>(t + j, tsrc + j);
+            }
+        }
+        cp_async_commit();
+    };
+    if (!fw) {
+        for (int q = tt; q < ny; q += kPipeT) state[q] = {0.f, 0.f};
+        issue(0);
+        cp_async_wait<0>();
+    }
+    __syncthreads();
+    for (int it = 0; it <= nz; ++it) {
+        if (fw) {
+            if (it < nz) fft1_warp_fwd(fb(it), sstride, N1, N2, fN1, fN2, twy, tid);
+        } else {
+            issue(it + 1);
+            if (it >= 1) {
+                const int k = it - 1;
+                const cx<float> *buf = fb(k);
+                const float *t = tb(k);
+                cx<float> *pl = specw + ((size_t)k * ncb + cb) * ny;
+                const float a = az[k];
+                for (int q = tt; q < ny; q += kPipeT) {
+                    const cx<float> rin = buf[pos_nat(q, fN2)];
+                    const float inv = t[q];
+                    const cx<float> dp = state[q];
+                    cx<float> d = {(rin.x - a * dp.x) * inv, (rin.y - a * dp.y) * inv};
+                    if (cb == 0 && q == 0) d = rin;  // (0,0) mode: solved by k_00
+                    state[q] = d;
+                    pl[q] = d;
+                }
+            }
+            cp_async_wait<0>();  // plane it+1 is in its ring entry (this thread's copies)
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void yzbwd_pipe(const Work &w, const GridDev &G, int cb, unsigned char *smem) {
+    const int ny = G.ny, nz = G.nz, ncb = G.ncb;
+    const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fny1, fN2 = G.fny2;
+    const size_t fstage = pipe_align16((size_t)sstride * 8), tstage = pipe_align16((size_t)ny * 4);
+    auto fb = [&](int i) { return reinterpret_cast<cx<float> *>(smem + (size_t)(i % kPipeB) * fstage); };
+    auto tb = [&](int i) { return reinterpret_cast<float *>(smem + kPipeB * fstage + (size_t)(i % 2) * tstage); };
+    cx<float> *state = reinterpret_cast<cx<float> *>(smem + kPipeB * fstage + 2 * tstage);
+    cx<float> *spec = reinterpret_cast<cx<float> *>(w.spec) + G.spec_off;
+    const float *tab = reinterpret_cast<const float *>(w.tab) + G.tab_off;
+    const cx<float> *twy = reinterpret_cast<const cx<float> *>(w.twy) + G.twy_off;
+    const float *cz = w.z.czf + G.z_off;
+    const int tid = threadIdx.x, tt = tid - 32;
+    const bool fw = tid < 32;
+    auto plane_of = [&](int i) { return nz - 1 - i; };  // i-th plane from the top
+    auto issue = [&](int i) {  // d' (slot q to the FFT position of slot q) and pivots of plane i
+        if (i < nz) {
+            const int k = plane_of(i);
+            cx<float> *f = fb(i);
+            float *t = tb(i);
+            const cx<float> *src = spec + ((size_t)k * ncb + cb) * ny;
+            const float *tsrc = tab + ((size_t)k * ncb + cb) * ny;
+            for (int q = tt; q < ny; q += kPipeT) {
+                cp_async<8>(f + pos_nat(q, fN2), src + q);
+                cp_async<4>(t + q, tsrc + q);
+            }
+        }
+        cp_async_commit();
+    };
+    if (!fw) {
+        for (int q = tt; q < ny; q += kPipeT) state[q] = {0.f, 0.f};
+        issue(0);
+        cp_async_wait<0>();
+    }
+    __syncthreads();
+    for (int it = 0; it <= nz + 1; ++it) {
+        if (fw) {
+            if (it >= 1 && it <= nz) fft1_warp_inv(fb(it - 1), sstride, N1, N2, fN1, fN2, twy, tid);
+        } else {
+            issue(it + 1);
+            if (it < nz) {  // back substitution of plane it, in place in its FFT buffer
+                const int k = plane_of(it);
+                cx<float> *buf = fb(it);
+                const float *t = tb(it);
+                const float c = cz[k];
+                for (int q = tt; q < ny; q += kPipeT) {
+                    const int pos = pos_nat(q, fN2);
+                    const cx<float> d = buf[pos];
+                    const float cp = c * t[q];
+                    const cx<float> nx_ = state[q];
+                    cx<float> ph = {d.x - cp * nx_.x, d.y - cp * nx_.y};
+                    if (cb == 0 && q == 0) ph = d;
+                    state[q] = ph;
+                    buf[pos] = ph;
+                }
+            }
+            if (it >= 2) {  // store plane it-2, transformed by warp 0 in the last iteration
+                const int k = plane_of(it - 2);
+                const cx<float> *buf = fb(it - 2);
+                cx<float> *pl = spec + ((size_t)k * ncb + cb) * ny;
+                for (int j = tt; j < ny; j += kPipeT) pl[j] = buf[pos_nat(j, fN2)];
+            }
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+    }
+}
+
 // y-FFT + Thomas forward elimination of one column block, sweeping k = 0..nz-1.
 // Shared memory: kYZStages x [FFT buffer (mb padded sequences) | pivot chunk], then the
 // Thomas state d'_{k-1} of every mode of the block.  Plane k+1 (spectrum and pivots)
@@ -70,6 +230,12 @@ __global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 
     const int g = find_grid(w.ystr_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
     const int cb = blockIdx.x - __ldg(w.ystr_start + g);
+    if constexpr (sizeof(T) == 4) {
+        if (G.mb == 1 && !(W && G.wall_y)) {
+            yzfwd_pipe(w, G, cb, smem_raw);
+            return;
+        }
+    }
     const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
     const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
@@ -145,6 +311,12 @@ __global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 
     const int g = find_grid(w.ystr_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
     const int cb = blockIdx.x - __ldg(w.ystr_start + g);
+    if constexpr (sizeof(T) == 4) {
+        if (G.mb == 1 && !(W && G.wall_y)) {
+            yzbwd_pipe(w, G, cb, smem_raw);
+            return;
+        }
+    }
     const int ny = G.ny, nz = G.nz, mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
     const FDiv fN1 = G.fny1, fN2 = G.fny2, fmb = G.fmb;
