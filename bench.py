@@ -44,11 +44,14 @@ BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of each
 # kernel from one ncu capture (512x512x128 mixed, see profiles/), valid while the
 # kernel sources hash to SOURCES_SHA256; otherwise the roofline's traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.69, "x_forward_residual": 15.23, "correct": 64.76,
-                          "yz_forward": 8.43, "yz_backward": 8.41, "x_inverse_store": 6.56,
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.67, "x_forward_residual": 15.26, "correct": 64.76,
+                          "yz_forward": 8.39, "yz_backward": 8.41, "x_inverse_store": 6.55,
                           "x_inverse_accumulate": 6.56}
-NCU_SOURCES_SHA256 = "eda42e58ef5a419fb1878876d09c65a4e4b8a80acf08f176ab09ab30af4440f9"
-KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_common.cuh", "ibf_device.cuh", "ibf_internal.h")
+NCU_SOURCES_SHA256 = "85499934963a7fdbc0a05a204152698ecfe80d2b3158b86d865ad449d7b81f5e"
+KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
+                  "ibf_internal.h", "ibf_viscous.h")
+# the same for the viscous solve's kernels (mixed path)
+NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.32}
 
 
 def kernel_sources_sha256():
@@ -233,11 +236,14 @@ def measure_viscous(plan, ins, outs, K, W, ws, mixed, cells, hbm_peak):
                for k, (c, t) in prof.items()}
     dname, (dc, dt_) = max(((k, v) for k, v in prof.items() if k in VISC_BYTES), key=lambda kv: kv[1][1])
     achieved = VISC_BYTES[dname][col] * cells / (dt_ / dc * 1e-3) / 1e9
+    traffic = None
+    if mixed and dname in NCU_VISC_TRAFFIC_B_PER_CELL and NCU_SOURCES_SHA256 == kernel_sources_sha256():
+        traffic = NCU_VISC_TRAFFIC_B_PER_CELL[dname] * cells
     total_b = 3 * sum(b[col] for b in VISC_BYTES.values())
     return {"ms_per_solve": ms, "value": ws * cells / (ms * 1e-3), "unit": "cells/s (three components)",
             "bytes_per_cell_model": total_b, "hbm_frac": total_b * cells / (ms * 1e-3) / 1e9 / hbm_peak,
             "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak, "traffic": traffic,
                          "bytes_per_cell": VISC_BYTES[dname][col]},
             "kernels": kernels, "gpu_launches": int(sum(c for c, _ in prof.values()))}
 
