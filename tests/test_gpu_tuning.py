@@ -56,6 +56,9 @@ def oracle(g, u, v, w):
 GRIDS = [  # (nx, ny, nz, beta, wall_x, wall_y): power-of-two, odd and tiny nz; walls
     (48, 24, 16, 2.0, False, False), (32, 12, 17, 1.5, False, False), (24, 16, 5, 1.0, True, False),
     (16, 24, 9, 2.5, False, True), (12, 8, 1, 0.0, False, False),
+    # two and three planes: the pipelined y/z kernels (mixed, one x-mode per block) fill
+    # and drain their rings in fewer iterations than they hold
+    (16, 12, 2, 1.0, False, False), (24, 12, 3, 1.5, True, False),
 ]
 VARIANTS = [
     dict(yz_kernel=1, mb=1), dict(yz_kernel=1, mb=3), dict(yz_kernel=1, mb=8),
