@@ -263,9 +263,9 @@ def viscous_oracle_sample(nx, ny, nz_sample):
             "sample": f"fp64 numpy oracle (Thomas + Sherman-Morrison per line) on {nx}x{ny}x{nz_sample}, {sec:.1f} s"}
 
 
-def workload_config(nx, ny, nz, refine):
+def workload_config(nx, ny, nz, refine, zbeta=BETA):
     return {"workload": f"{nx}x{ny}x{nz} staggered projection, periodic x,y (2pi), walls z in [0,2], "
-                        f"tanh beta {BETA}; velocity = k^-5/3 Fourier modes + U[-0.01,0.01] noise (seed {SEED}); "
+                        f"tanh beta {zbeta}{' (uniform z)' if zbeta == 0 else ''}; velocity = k^-5/3 Fourier modes + U[-0.01,0.01] noise (seed {SEED}); "
                         f"mixed precision (fp32 transforms/sweeps, float-float stencils, fp64 I/O), "
                         f"{refine} refinement sweep(s)",
             "grid": [nx, ny, nz], "refine_steps": refine}
@@ -377,7 +377,7 @@ def bench_batch64(args):
     kinds = {}
     for gi in range(len(grids)):
         t = plan.tuning(gi)
-        key = {1: "streaming", 2: "slab", 3: "split"}[t["yz_kernel"]]
+        key = {1: "streaming", 2: "slab", 3: "split", 4: "spectral_z"}[t["yz_kernel"]]
         kinds[key] = kinds.get(key, 0) + 1
     plan.close()
     if rank != 0:
@@ -402,6 +402,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", default="1024x1024x512")
+    ap.add_argument("--zbeta", type=float, default=BETA, help="tanh clustering of the z faces (0: uniform)")
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--ref-nz", type=int, default=4, help="z levels of the oracle sample per reference step")
     ap.add_argument("--cpu-nz", type=int, default=16, help="z levels of the cpu_baseline sample")
@@ -432,7 +433,7 @@ def main():
 
     nx, ny, nz = (int(x) for x in args.size.split("x"))
     cells = nx * ny * nz
-    g = Grid(nx, ny, nz, LX, LY, LZ, beta=BETA)
+    g = Grid(nx, ny, nz, LX, LY, LZ, beta=args.zbeta)
     dev = torch.device("cuda", torch.cuda.current_device())
     us, vs, ws_ = synth.kolmogorov_velocity_torch(SEED, nx, ny, nz, dev)
     ins = (us, vs, ws_)
@@ -489,7 +490,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(nx, ny, nz, args.refine), **{
+        "config": dict(workload_config(nx, ny, nz, args.refine, args.zbeta), **{
                    "parallelism": "replicas" if ws > 1 else "1 GPU",
                    "launch_shape": mixed["tuning"], "autotuned": bool(args.autotune),
                    "l2_policy": l2_policy}),

@@ -207,7 +207,11 @@ ibf_status ibf_viscous_solve(ibf_plan *plan, const ibf_fields *in, const ibf_fie
  *               (the whole z extent of a column block in shared memory: one read,
  *               one write; small grids only), 3 split (y-FFT of every (plane, column
  *               block) in its own CTA, then Thomas sweeps with one thread per mode:
- *               the spectrum read and written four times, all of it streamed);
+ *               the spectrum read and written four times, all of it streamed),
+ *               4 spectral z (uniform z with Neumann walls at both ends only, nz a
+ *               product of two FFT sizes: the y-FFTs of 3, then per z line a DCT-II
+ *               along z, division by the mode's eigenvalue, inverse DCT; no
+ *               tridiagonal sweep; INVALID_ARG on a stretched z or an outlet);
  *   mb        : x-modes per column block of the y/z kernels;
  *   tri       : tridiagonal algorithm of the slab kernel: 1 Thomas per mode with the
  *               plan's pivot table, 1 + S (S >= 1) S levels of in-place cyclic

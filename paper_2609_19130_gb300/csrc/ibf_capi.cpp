@@ -76,7 +76,8 @@ struct ibf_plan {
     std::vector<GridHost> grids;
     std::vector<void *> allocs;
     Work work{};
-    size_t xsmem = 0, yzsmem = 0, slabsmem = 0, yfftsmem = 0;
+    size_t xsmem = 0, yzsmem = 0, slabsmem = 0, yfftsmem = 0, zdctsmem = 0;
+    int nzdctblk = 0;
     // viscous solve: pivots of (I - beta Lz) per grid (6 (nz+1) entries at 6 z_off) and the
     // shared memory of its y kernel
     double *helm = nullptr, *fxy = nullptr;
@@ -238,12 +239,12 @@ int ilog2_floor(int n) {
 
 // Shared memory of the kernels for one grid under a launch shape.
 struct SmemNeed {
-    size_t x, yz, slab, yfft;
+    size_t x, yz, slab, yfft, zdct;
 };
 SmemNeed smem_need(const ibf_grid &g, int mixed, const ibf_tuning &t) {
     const size_t csz = mixed ? 8 : 16, rsz = mixed ? 4 : 8;
     const int nx2 = g.nx / t.x_n1, ny2 = g.ny / t.y_n1;
-    SmemNeed n{0, 0, 0, 0};
+    SmemNeed n{0, 0, 0, 0, 0};
     n.x = (size_t)(t.rows / 2) * (size_t)(t.x_n1 * (nx2 + 1) + 1) * csz;
     const size_t sstr = (size_t)(t.y_n1 * (ny2 + 1) + 1), nslot = (size_t)g.ny * t.mb;
     if (t.yz_kernel == 1) {  // layouts of k_yzfwd / k_yzbwd
@@ -256,8 +257,22 @@ SmemNeed smem_need(const ibf_grid &g, int mixed, const ibf_tuning &t) {
         if (t.tri > 1) n.slab += 3 * (size_t)g.nz * nslot * rsz;
     } else {
         n.yfft = (size_t)t.mb * sstr * csz;
+        if (t.yz_kernel == 4) {  // k_zdct: zdct lines of the padded z sequence
+            int a = 1, b = 1;
+            factor(g.nz, &a, &b);
+            n.zdct = (size_t)(mixed ? kZdctLinesF32 : kZdctLinesF64) * (size_t)(a * (b + 1) + 1) * csz;
+        }
     }
     return n;
+}
+
+// z faces equally spaced (to 1e-12 of lz): the spectral-z path applies
+bool z_uniform(const std::vector<double> &zf) {
+    const int nz = (int)zf.size() - 1;
+    const double lz = zf[nz] - zf[0];
+    for (int k = 0; k <= nz; ++k)
+        if (std::fabs(zf[k] - zf[0] - lz * (double)k / nz) > 1e-12 * lz) return false;
+    return true;
 }
 
 bool fft_pair_ok(int n, int n1) { return n1 >= 1 && n % n1 == 0 && in_sizes(n1) && in_sizes(n / n1); }
@@ -266,7 +281,7 @@ bool fft_pair_ok(int n, int n1) { return n1 >= 1 && n % n1 == 0 && in_sizes(n1) 
 // the others.  The defaults: x kernels ~64 KB of FFT rows per CTA; balanced FFT
 // factors; streaming y/z kernels with enough x-modes per block for 64+ FFT tasks per
 // pass but at least one block per SM over the batch; Thomas with the pivot table.
-ibf_status resolve_tuning(const ibf_grid &g, int mixed, long long total_cols, int nsm, size_t cap,
+ibf_status resolve_tuning(const ibf_grid &g, bool zuni, int mixed, long long total_cols, int nsm, size_t cap,
                           ibf_tuning *t) {
     const int nxh = x_modes(g);
     const int ny_even = (g.ny + 1) & ~1;
@@ -281,7 +296,11 @@ ibf_status resolve_tuning(const ibf_grid &g, int mixed, long long total_cols, in
     if (t->rows & 1) return IBF_ERR_UNSUPPORTED_SIZE;
     t->rows = std::min(t->rows, std::max(2, ny_even));
     if (t->yz_kernel <= 0) t->yz_kernel = 1;
-    if (t->yz_kernel > 3) return IBF_ERR_INVALID_ARG;
+    if (t->yz_kernel > 4) return IBF_ERR_INVALID_ARG;
+    if (t->yz_kernel == 4) {  // spectral z: uniform z, Neumann at both ends, nz = n1 n2 in the FFT sizes
+        int a, b;
+        if (!zuni || g.bc_zhi != IBF_BC_NEUMANN || !factor(g.nz, &a, &b)) return IBF_ERR_INVALID_ARG;
+    }
     if (t->mb <= 0) {
         const int ny2 = g.ny / t->y_n1;
         const int mbmax = std::max(1, std::min(nxh, 4096 / g.ny));
@@ -295,7 +314,7 @@ ibf_status resolve_tuning(const ibf_grid &g, int mixed, long long total_cols, in
     if (t->tri <= 0) t->tri = 1;
     if (t->tri > 1 + ilog2_floor(g.nz)) return IBF_ERR_INVALID_ARG;
     const SmemNeed n = smem_need(g, mixed, *t);
-    if (n.x > cap || n.yz > cap || n.slab > cap || n.yfft > cap) return IBF_ERR_UNSUPPORTED_SIZE;
+    if (n.x > cap || n.yz > cap || n.slab > cap || n.yfft > cap || n.zdct > cap) return IBF_ERR_UNSUPPORTED_SIZE;
     return IBF_OK;
 }
 
@@ -313,9 +332,9 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     for (int g = 0; g < ngrids; ++g) total_cols += x_modes(grids[g]);
 
     long long spec = 0, cells = 0;
-    int zoff = 0, poff = 0, xblk = 0, yzblk = 0, strblk = 0, slabblk = 0, yfftblk = 0, sweepblk = 0;
+    int zoff = 0, poff = 0, xblk = 0, yzblk = 0, strblk = 0, slabblk = 0, yfftblk = 0, sweepblk = 0, zdctblk = 0;
     std::vector<int> str_start(ngrids + 1, 0), slab_start(ngrids + 1, 0), yfft_start(ngrids + 1, 0),
-        sweep_start(ngrids + 1, 0);
+        sweep_start(ngrids + 1, 0), zdct_start(ngrids + 1, 0);
     std::vector<double> twx_all, twy_all, tmp;
     size_t maxx = 0, maxyz = 0, maxslab = 0, maxyfft = 0;
     for (int g = 0; g < ngrids; ++g) {
@@ -334,7 +353,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         d.nyv = d.ny + d.wall_y;
         ibf_tuning &t = H.tun;
         t = tuning ? tuning[g] : ibf_tuning{0, 0, 0, 0, 0, 0};
-        IBF_TRY(resolve_tuning(H.g, mixed, total_cols, nsm, smem_cap(prop), &t));
+        IBF_TRY(resolve_tuning(H.g, z_uniform(H.zf), mixed, total_cols, nsm, smem_cap(prop), &t));
         d.nx1 = t.x_n1; d.nx2 = d.nx / t.x_n1;
         d.ny1 = t.y_n1; d.ny2 = d.ny / t.y_n1;
         d.mb = t.mb;
@@ -382,7 +401,22 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
             slabblk += d.ncb;
         } else {
             yfftblk += d.nz * d.ncb;
-            sweepblk += (int)(((long long)d.ncb * d.ny * d.mb + kSweepThreads - 1) / kSweepThreads);
+            if (d.yzk == 2)
+                sweepblk += (int)(((long long)d.ncb * d.ny * d.mb + kSweepThreads - 1) / kSweepThreads);
+        }
+        zdct_start[g] = zdctblk;
+        if (d.yzk == 3) {
+            const int lines = mixed ? kZdctLinesF32 : kZdctLinesF64;
+            zdctblk += (int)(((long long)d.ncb * d.ny * d.mb + lines - 1) / lines);
+            factor(d.nz, &d.nz1, &d.nz2);
+            d.fnz1 = make_fdiv(d.nz1);
+            d.fnz2 = make_fdiv(d.nz2);
+            d.twz_off = (int)(twy_all.size() / 2);
+            twiddles(d.nz, d.nz1, tmp);
+            twy_all.insert(twy_all.end(), tmp.begin(), tmp.end());
+            d.dctz_off = (int)(twy_all.size() / 2);
+            dct_twiddles(d.nz, tmp);
+            twy_all.insert(twy_all.end(), tmp.begin(), tmp.end());
         }
         d.dx = H.g.lx / d.nx; d.dy = H.g.ly / d.ny;
         d.rdx = 1.0 / d.dx; d.rdy = 1.0 / d.dy;
@@ -404,6 +438,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
             maxyz = std::max(maxyz, n.yz);
             maxslab = std::max(maxslab, n.slab);
             maxyfft = std::max(maxyfft, n.yfft);
+            pl->zdctsmem = std::max(pl->zdctsmem, n.zdct);
             const size_t csz = mixed ? 8 : 16;
             pl->helmsmem = std::max(pl->helmsmem, (size_t)(yhelm_group(t.mb) * t.mb) *
                                                       (size_t)(t.y_n1 * (d.ny2 + 1) + 1) * csz);
@@ -413,12 +448,15 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     }
     const size_t cap = smem_cap(prop);
     pl->smemcap = cap;
-    if (maxx > cap || maxyz > cap || maxslab > cap || maxyfft > cap || (size_t)10 * (pl->maxnz + 1) * 8 > cap)
+    if (maxx > cap || maxyz > cap || maxslab > cap || maxyfft > cap || pl->zdctsmem > cap ||
+        (size_t)10 * (pl->maxnz + 1) * 8 > cap)
         return IBF_ERR_UNSUPPORTED_SIZE;
     str_start[ngrids] = strblk;
     slab_start[ngrids] = slabblk;
     yfft_start[ngrids] = yfftblk;
     sweep_start[ngrids] = sweepblk;
+    zdct_start[ngrids] = zdctblk;
+    pl->nzdctblk = zdctblk;
     pl->yfftsmem = maxyfft;
     pl->nyfftblk = yfftblk;
     pl->nsweepblk = sweepblk;
@@ -484,15 +522,17 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     GridDev *dgrids;
     IBF_TRY(dalloc(pl, &dgrids, sizeof(GridDev) * ngrids));
     w.grids = dgrids;
-    int *dx, *dyz, *dstr, *dslab, *dyfft, *dsweep;
+    int *dx, *dyz, *dstr, *dslab, *dyfft, *dsweep, *dzdct;
     IBF_TRY(dalloc(pl, &dx, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dyz, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dstr, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dslab, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dyfft, sizeof(int) * (ngrids + 1)));
     IBF_TRY(dalloc(pl, &dsweep, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(dalloc(pl, &dzdct, sizeof(int) * (ngrids + 1)));
     w.yfft_start = dyfft;
     w.sweep_start = dsweep;
+    w.zdct_start = dzdct;
     w.xblk_start = dx;
     w.yzblk_start = dyz;
     w.ystr_start = dstr;
@@ -560,6 +600,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     IBF_TRY(upload(slab_start.data(), dslab, sizeof(int) * (ngrids + 1)));
     IBF_TRY(upload(yfft_start.data(), dyfft, sizeof(int) * (ngrids + 1)));
     IBF_TRY(upload(sweep_start.data(), dsweep, sizeof(int) * (ngrids + 1)));
+    IBF_TRY(upload(zdct_start.data(), dzdct, sizeof(int) * (ngrids + 1)));
     IBF_TRY(upload(hz.data(), w.z.hz, sizeof(double) * nzt));
     IBF_TRY(upload(rhz.data(), w.z.rhz, sizeof(double) * nzt));
     IBF_TRY(upload(rgzf.data(), w.z.rgzf, sizeof(double) * nzt));
@@ -671,13 +712,17 @@ ibf_status solve_core(Ctx &c, int first) {
         IBF_TRY(timed(c, "yz_forward", [&]() { return launch_yzfwd(pl->mixed, w, pl->nstrblk, pl->yzsmem, c.st); }));
     if (pl->nyfftblk > 0) {
         IBF_TRY(timed(c, "y_fft_forward", [&]() { return launch_yfft(pl->mixed, 0, w, pl->nyfftblk, pl->yfftsmem, c.st); }));
-        IBF_TRY(timed(c, "z_sweep_forward", [&]() { return launch_zsweep(pl->mixed, 0, w, pl->nsweepblk, c.st); }));
+        if (pl->nsweepblk > 0)
+            IBF_TRY(timed(c, "z_sweep_forward", [&]() { return launch_zsweep(pl->mixed, 0, w, pl->nsweepblk, c.st); }));
     }
+    if (pl->nzdctblk > 0)  // spectral z: DCT along z, division, inverse DCT (before k_00 writes the (0,0) column)
+        IBF_TRY(timed(c, "z_dct_solve", [&]() { return launch_zdct(pl->mixed, w, pl->nzdctblk, pl->zdctsmem, c.st); }));
     IBF_TRY(timed(c, "mode00", [&]() { return launch_k00(w, pl->mixed, first, pl->maxnz, c.st); }));
     if (pl->nstrblk > 0)
         IBF_TRY(timed(c, "yz_backward", [&]() { return launch_yzbwd(pl->mixed, w, pl->nstrblk, pl->yzsmem, c.st); }));
     if (pl->nyfftblk > 0) {
-        IBF_TRY(timed(c, "z_sweep_backward", [&]() { return launch_zsweep(pl->mixed, 1, w, pl->nsweepblk, c.st); }));
+        if (pl->nsweepblk > 0)
+            IBF_TRY(timed(c, "z_sweep_backward", [&]() { return launch_zsweep(pl->mixed, 1, w, pl->nsweepblk, c.st); }));
         IBF_TRY(timed(c, "y_fft_inverse", [&]() { return launch_yfft(pl->mixed, 1, w, pl->nyfftblk, pl->yfftsmem, c.st); }));
     }
     if (pl->nslabblk > 0)
@@ -775,8 +820,8 @@ ibf_status make_plan(ibf_plan **plan, const ibf_grid *grids, int ngrids, const i
 // algorithm that fits shared memory).  Results are cached per (shape, boundary
 // conditions, precision, refinement, forced fields) for the life of the process.
 struct TuneKey {
-    int v[14];
-    bool operator<(const TuneKey &o) const { return std::lexicographical_compare(v, v + 14, o.v, o.v + 14); }
+    int v[15];
+    bool operator<(const TuneKey &o) const { return std::lexicographical_compare(v, v + 15, o.v, o.v + 15); }
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, ibf_tuning> g_tune_cache;
@@ -816,10 +861,13 @@ float time_shape(TuneBench &b, const ibf_tuning &t) {
 }
 
 ibf_status tune_grid(const ibf_grid &g, const ibf_opts &opts, int device, ibf_tuning *t) {
+    std::vector<double> zf;
+    IBF_TRY(validate(&g, zf));
+    const bool zuni = z_uniform(zf);
     TuneKey key;
-    const int kv[14] = {g.nx, g.ny, g.nz, g.bc_x, g.bc_y, g.bc_zhi, opts.precision, opts.refine_steps,
-                        t->rows, t->x_n1, t->y_n1, t->yz_kernel, t->mb, t->tri};
-    std::copy(kv, kv + 14, key.v);
+    const int kv[15] = {g.nx, g.ny, g.nz, g.bc_x, g.bc_y, g.bc_zhi, opts.precision, opts.refine_steps,
+                        t->rows, t->x_n1, t->y_n1, t->yz_kernel, t->mb, t->tri, zuni ? 1 : 0};
+    std::copy(kv, kv + 15, key.v);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -863,7 +911,7 @@ ibf_status tune_grid(const ibf_grid &g, const ibf_opts &opts, int device, ibf_tu
             cudaDeviceProp prop;
             cudaGetDeviceProperties(&prop, device);
             ibf_tuning d = forced;
-            if (resolve_tuning(g, opts.precision == IBF_MIXED, x_modes(g), prop.multiProcessorCount,
+            if (resolve_tuning(g, zuni, opts.precision == IBF_MIXED, x_modes(g), prop.multiProcessorCount,
                                smem_cap(prop), &d) == IBF_OK)
                 consider(d);
         }
@@ -881,8 +929,11 @@ ibf_status tune_grid(const ibf_grid &g, const ibf_opts &opts, int device, ibf_tu
                     if (n1 != best.y_n1 && fft_pair_ok(g.ny, n1)) { ibf_tuning c2 = best; c2.y_n1 = n1; consider(c2); }
             const ibf_tuning base = best;
             const int nxh = x_modes(g);
-            for (int kern = 1; kern <= 3; ++kern) {
+            int a1, b1;
+            const bool spectral_ok = zuni && g.bc_zhi == IBF_BC_NEUMANN && factor(g.nz, &a1, &b1);
+            for (int kern = 1; kern <= 4; ++kern) {
                 if (forced.yz_kernel > 0 && forced.yz_kernel != kern) continue;
+                if (kern == 4 && !spectral_ok) continue;
                 for (int mb : kMb) {
                     if (mb > nxh && mb != 1) continue;
                     if (forced.mb > 0 && forced.mb != mb) continue;
@@ -963,7 +1014,11 @@ ibf_status ibf_projection_plan_tuned(ibf_plan **plan, const ibf_grid *grids, int
         if (s != IBF_OK) return s;
         if (tuning) {
             const ibf_tuning &t = tuning[g];
-            if (t.yz_kernel > 3 || (t.rows > 0 && (t.rows & 1))) return IBF_ERR_INVALID_ARG;
+            if (t.yz_kernel > 4 || (t.rows > 0 && (t.rows & 1))) return IBF_ERR_INVALID_ARG;
+            int a, b;
+            if (t.yz_kernel == 4 &&
+                (!z_uniform(zf) || grids[g].bc_zhi != IBF_BC_NEUMANN || !factor(grids[g].nz, &a, &b)))
+                return IBF_ERR_INVALID_ARG;  // spectral z: uniform z, Neumann top, nz a product of FFT sizes
         }
     }
     cudaError_t e = cudaSetDevice(device);

@@ -28,6 +28,8 @@ inline size_t yz_pipe_smem(int ny, int sstr) {
 }
 constexpr int kSlabThreads = 256;  // resident-slab y/z kernel
 constexpr int kSweepThreads = 256; // split y/z path: Thomas sweeps, one thread per mode
+// spectral z: z lines (slots of a plane) per k_zdct CTA, mixed / fp64
+constexpr int kZdctLinesF32 = 16, kZdctLinesF64 = 8;
 
 // Division by a run-time invariant d (Granlund & Montgomery, PLDI 1994, round-up
 // variant): n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31.
@@ -44,7 +46,10 @@ struct GridDev {
     int dir_top;               // 1: homogeneous Dirichlet phi on the top face (outlet), else Neumann
     double ez_top;             // Dirichlet outlet: extra diagonal of level nz-1, rhz / (lz - zc_{nz-1})
     int yzk;                   // y/z kernels: 0 streaming (k_yzfwd + k_yzbwd), 1 resident slab (k_yzslab),
-                               // 2 split (k_yfft, k_zsweep_fwd / k_zsweep_bwd)
+                               // 2 split (k_yfft, k_zsweep_fwd / k_zsweep_bwd), 3 spectral z (k_yfft,
+                               // k_zdct: DCT along z, uniform z with Neumann walls)
+    int nz1, nz2;              // spectral z: two-level FFT factors of nz
+    int twz_off, dctz_off;     // spectral z: four-step and DCT twiddles of nz (in twy)
     int cr_levels;             // slab kernel: cyclic-reduction levels before Thomas (0: Thomas with the table)
     int nx1, nx2, ny1, ny2;    // two-level FFT factors: nx = nx1*nx2, ny = ny1*ny2
     int mb, ncb;               // x-modes per column block of the yz kernels, number of blocks
@@ -61,6 +66,7 @@ struct GridDev {
     double sum_hz;             // lz
     FDiv fnx, fnx1, fnx2, fny1, fny2, fmb, frows, fnpair, fnph;  // fnph: nx/2 + 1
     FDiv fnpair2;              // rows / 4 (row pairs of the half-block CTAs of the inverse x-FFT)
+    FDiv fnz1, fnz2;           // spectral z: nz1, nz2
 };
 
 // Per-level arrays (index z_off + k; nz+1 entries per grid, the last one only used where noted).
@@ -86,6 +92,7 @@ struct Work {
     const int *slab_start;     // prefix of column blocks over grids with the resident-slab kernel
     const int *yfft_start;     // split path: prefix of (plane, column block) FFT blocks over grids
     const int *sweep_start;    // split path: prefix of Thomas-sweep blocks (kSweepThreads modes each)
+    const int *zdct_start;     // spectral z: prefix of k_zdct blocks (zdct_lines(T) z lines each)
     double *sol00;             // per level (z_off + k): solution of the (0,0) mode, written by k_00
     ZArrays z;
     void *spec;                // complex<T> spectrum, per grid nz*ncb*ny*mb
@@ -129,6 +136,7 @@ cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cud
 cudaError_t launch_yzslab(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_yfft(int mixed, int inverse, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_zsweep(int mixed, int backward, const Work &w, int nblk, cudaStream_t st);
+cudaError_t launch_zdct(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
                         size_t smem, cudaStream_t st);
 cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,

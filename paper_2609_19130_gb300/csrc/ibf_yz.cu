@@ -791,6 +791,77 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     }
 }
 
+// ================================================================ spectral z
+// yz_kernel 4, uniform z with Neumann walls at both ends: the cell-centred second
+// difference along z is then diagonalised by the DCT-II (eigenvalues
+// -(4/hz^2) sin^2(pi l / (2 nz)), l < nz), so after the y transforms of the split path
+// every mode (m, n, l) is divided by lambda_x(m) + lambda_y(n) + lambda_z(l) and no
+// tridiagonal sweep remains.  The same slot of every plane's spectrum is one z line;
+// a CTA takes zdct_lines<T>() consecutive slots: DCT-II along z (Makhoul reorder, FFT,
+// post-twiddle), division, DCT-III (pre-twiddle, inverse FFT, un-reordering; the unscaled
+// pair returns nz times the input, folded into the division).  The (0,0) column is
+// overwritten afterwards by k_00 (fp64, compatibility and mean handling).
+template <typename T> __host__ __device__ constexpr int zdct_lines() { return sizeof(T) == 4 ? kZdctLinesF32 : kZdctLinesF64; }
+template <typename T> __device__ __forceinline__ T sinpi_T(T x);
+template <> __device__ __forceinline__ float sinpi_T<float>(float x) { return sinpif(x); }
+template <> __device__ __forceinline__ double sinpi_T<double>(double x) { return sinpi(x); }
+
+template <typename T>
+__global__ void __launch_bounds__(kYZThreads) k_zdct(Work w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TM = zdct_lines<T>();
+    const int g = find_grid(w.zdct_start, w.ngrids, blockIdx.x);
+    const GridDev &G = w.grids[g];
+    const int ny = G.ny, nz = G.nz, mb = G.mb;
+    const long long M = (long long)G.ncb * ny * mb;  // slots per plane
+    const long long s0 = (long long)(blockIdx.x - __ldg(w.zdct_start + g)) * TM;
+    const int N1 = G.nz1, N2 = G.nz2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fnz1, fN2 = G.fnz2;
+    const cx<T> *twz = reinterpret_cast<const cx<T> *>(w.twy) + G.twz_off;
+    const cx<T> *dctz = reinterpret_cast<const cx<T> *>(w.twy) + G.dctz_off;
+    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int t = tid; t < TM * nz; t += nthr) {  // plane k, line i: consecutive threads on consecutive slots
+        const int k = t / TM, i = t - k * TM;
+        const long long s = s0 + i;
+        buf[i * sstride + pos_nat(dct_perm(k, nz), fN2)] = s < M ? spec[(size_t)k * M + s] : cx<T>{(T)0, (T)0};
+    }
+    __syncthreads();
+    fft_batch<T, -1>(buf, TM, sstride, N1, N2, fN1, fN2, twz);
+    dct_post<T>(buf, TM, sstride, nz, N1, N2, fN1, dctz);
+    const T cx_ = (T)(4.0 * G.rdx * G.rdx), cy_ = (T)(4.0 * G.rdy * G.rdy);
+    const T cz_ = (T)(4.0 * nz * nz / (G.sum_hz * G.sum_hz));
+    const T dxn = (T)(G.wall_x ? 2 * G.nx : G.nx), dyn = (T)(G.wall_y ? 2 * ny : ny);
+    for (int t = tid; t < TM * nz; t += nthr) {
+        const int i = t / nz, l = t - i * nz;
+        const long long s = s0 + i;
+        cx<T> &v = buf[i * sstride + pos_tr(l, N1, N2, fN1)];
+        T f = (T)0;
+        if (s < M) {
+            const int mm = (int)(s % mb);
+            const long long rest = s / mb;
+            const int j = (int)(rest % ny), cb = (int)(rest / ny);
+            const int m = cb * mb + mm, n = (j / G.ny2) + G.ny1 * (j % G.ny2);  // slot row j holds y-mode n
+            if (m < G.nxh) {
+                const T sx = sinpi_T<T>((T)m / dxn), sy = sinpi_T<T>((T)n / dyn),
+                        sz = sinpi_T<T>((T)l / (T)(2 * nz));
+                const T lam = -(cx_ * sx * sx + cy_ * sy * sy + cz_ * sz * sz);
+                if (lam != (T)0) f = (T)1 / (lam * (T)nz);
+            }
+        }
+        v = {v.x * f, v.y * f};
+    }
+    __syncthreads();
+    dct_pre<T>(buf, TM, sstride, nz, N1, N2, fN1, dctz);
+    fft_batch<T, +1>(buf, TM, sstride, N1, N2, fN1, fN2, twz);
+    for (int t = tid; t < TM * nz; t += nthr) {
+        const int k = t / TM, i = t - k * TM;
+        const long long s = s0 + i;
+        if (s < M) spec[(size_t)k * M + s] = buf[i * sstride + pos_nat(dct_perm(k, nz), fN2)];
+    }
+}
+
 // Pivots of every mode's tridiagonal system (fp64 arithmetic, stored as T):
 // inv_k = 1/(bz_k + lambda - az_k c'_{k-1}),  c'_k = cz_k inv_k,  bz_k = -(az_k + cz_k),
 // lambda = -4/dx^2 sin^2(pi m/nx) - 4/dy^2 sin^2(pi n/ny), with pi m/(2 nx), pi n/(2 ny)
@@ -911,6 +982,13 @@ cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_zdct(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st) {
+    if (nblk <= 0) return cudaSuccess;
+    if (mixed) k_zdct<float><<<grid1(nblk), kYZThreads, smem, st>>>(w);
+    else k_zdct<double><<<grid1(nblk), kYZThreads, smem, st>>>(w);
+    return cudaGetLastError();
+}
+
 cudaError_t set_smem_limits_yz(int mixed) {
     cudaError_t e = cudaSuccess;
     auto set = [&](const void *fn) {
@@ -936,6 +1014,8 @@ cudaError_t set_smem_limits_yz(int mixed) {
     set_all(std::true_type{});
     if (mixed) set((const void *)k_00<float>);
     else set((const void *)k_00<double>);
+    if (mixed) set((const void *)k_zdct<float>);
+    else set((const void *)k_zdct<double>);
     return e;
 }
 

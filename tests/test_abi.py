@@ -113,11 +113,12 @@ def test_valid_plan_without_gpu_reports_cuda_error(lib):
     assert N.last_error()
 
 
-@pytest.mark.parametrize("bad", [dict(rows=3), dict(yz_kernel=4)])
-def test_tuning_validation_on_host(lib, bad):
+@pytest.mark.parametrize("bad,beta", [(dict(rows=3), 0.0), (dict(yz_kernel=5), 0.0),
+                                      (dict(yz_kernel=4), 1.5)])  # spectral z needs a uniform z
+def test_tuning_validation_on_host(lib, bad, beta):
     """Forced launch shapes are checked on the host before the device is touched."""
     g = (N.ibf_grid * 1)()
-    g[0] = N.ibf_grid(16, 16, 8, 1.0, 1.0, 1.0, None, 0.0, 0, 0, 1, 1)
+    g[0] = N.ibf_grid(16, 16, 8, 1.0, 1.0, 1.0, None, beta, 0, 0, 1, 1)
     t = (N.ibf_tuning * 1)()
     t[0] = N.ibf_tuning(*(bad.get(f, 0) for f in N.TUNING_FIELDS))
     h = C.c_void_p()

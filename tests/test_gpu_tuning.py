@@ -113,7 +113,8 @@ def test_invalid_tunings_rejected():
     g = Grid(24, 16, 8, 1.0, 1.0, 1.0, beta=1.0)
     for bad, status in ((dict(x_n1=5), N.IBF_ERR_UNSUPPORTED_SIZE),     # 5 does not divide 24
                         (dict(tri=9), N.IBF_ERR_INVALID_ARG),           # > 1 + log2(8)
-                        (dict(yz_kernel=4), N.IBF_ERR_INVALID_ARG),
+                        (dict(yz_kernel=4), N.IBF_ERR_INVALID_ARG),     # spectral z on a stretched z
+                        (dict(yz_kernel=5), N.IBF_ERR_INVALID_ARG),
                         (dict(rows=3), N.IBF_ERR_INVALID_ARG)):         # rows must be even
         with pytest.raises(IBFError) as ei:
             Plan([g], precision=MIXED, tuning=[bad])
