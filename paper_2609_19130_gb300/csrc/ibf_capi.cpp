@@ -285,7 +285,7 @@ ibf_status resolve_tuning(const ibf_grid &g, bool zuni, int mixed, long long tot
                           ibf_tuning *t) {
     const int nxh = x_modes(g);
     const int ny_even = (g.ny + 1) & ~1;
-    int a, b;
+    int a = 1, b = 1;  // nx and ny factor (validate checked them)
     if (t->x_n1 <= 0) { factor(g.nx, &a, &b); t->x_n1 = a; }
     if (t->y_n1 <= 0) { factor(g.ny, &a, &b); t->y_n1 = a; }
     if (!fft_pair_ok(g.nx, t->x_n1) || !fft_pair_ok(g.ny, t->y_n1)) return IBF_ERR_UNSUPPORTED_SIZE;
