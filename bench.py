@@ -35,8 +35,11 @@ LZ = 2.0
 BETA = 2.5
 DT = 1e-3
 SEED = 4
-# Algorithmic HBM bytes per cell of each kernel (fp64 user fields, fp32 spectrum,
-# float-float right-hand side); derivation in the design doc.
+# Algorithmic HBM bytes per cell of each kernel (fp64 user fields, fp32 spectrum of
+# ~4 B per cell, float-float right-hand side): x_forward_div reads u*, v*, w* (24) and
+# writes b (8) and the spectrum (4); a y/z pass reads and writes the spectrum and reads
+# the fp32 pivot table (4 + 4 + 2); the residual reads phi_0 and b (4 + 8) and writes the
+# spectrum; the correction reads u*, v*, w*, phi (24 + 8) and writes u, v, w, phi (24 + 8).
 BYTES_MIXED = {"x_forward_div": 36.0, "yz_forward": 10.0, "yz_backward": 10.0, "x_inverse_store": 8.0,
                "x_forward_residual": 16.0, "x_inverse_accumulate": 16.0, "correct": 64.0, "mode00": 0.0}
 BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x_inverse_store": 16.0,

@@ -21,7 +21,7 @@
  * tridiagonal system is solved with the textbook Thomas algorithm, in FP64,
  * one real system for the real part and one for the imaginary part.
  *
- * Readings taken where the paper is silent (each listed in the design doc):
+ * Readings taken where the paper is silent:
  *  R1 index convention: cells i<nx, j<ny, k<nz; u[k][j][i] sits on the x-face
  *     at x = i dx (face i is the left face of cell i), v on the y-face at
  *     y = j dy, w[k][j][i] on the z-face z = zf[k], k = 0..nz (w[0], w[nz] are

@@ -1,6 +1,8 @@
 """Parity of the CUDA projection (through the C ABI) with the FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (the fp64 bounds are rounding of O(10) transform and sweep operations on
+values of size max|u*|; the mixed ones are the stated 1e-9, met after one refinement
+sweep, which leaves an error of about (fp32 error)^2 of the solve):
   FP64 path : relative L2 of phi <= 1e-12, velocity max error <= 1e-11 max|u*|,
               max|D u| <= 1e-11 max|D u*|;
   mixed path: relative L2 of phi <= 1e-9 after refinement, velocity max error
