@@ -64,9 +64,10 @@ typedef enum ibf_status {
     IBF_ERR_TIMEOUT = 5,          /* a bounded device wait gave up (reported by ibf_plan_sync_status) */
     IBF_ERR_NONFINITE = 6,        /* NaN or Inf met in the right-hand side (ibf_plan_sync_status) */
     IBF_WARN_INCOMPATIBLE_RHS = 7,/* |compatibility defect| above 1e-8 of the RHS scale; result still returned */
-    IBF_ERR_UNSUPPORTED_BC = 8    /* a boundary condition this build does not implement (Dirichlet in
+    IBF_ERR_UNSUPPORTED_BC = 8    /* a boundary condition the library does not implement (Dirichlet in
                                      x, y or at the bottom, periodic z; for ibf_project_noalloc also
-                                     walls in x or y and a Dirichlet outlet) */
+                                     walls in x or y and a Dirichlet outlet; for ibf_viscous_solve
+                                     walls in x or y) */
 } ibf_status;
 
 typedef enum ibf_bc {
