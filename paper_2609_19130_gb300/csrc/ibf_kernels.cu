@@ -584,7 +584,9 @@ constexpr int kRowGroupC = 2;
 //                    w_k = g_w,k + psi_{k-1} [k>=1] - psi_k [k<=nz-1].
 // PU: forward with a pressure update (pmode 1: p_n + phi, 2: minus cimp (b - <b>)).
 template <class A, int ADJ, bool W, bool PU>
-__global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 4 : 3)  // fp64: room for the pressure terms
+// mixed: five CTAs per SM (48 registers; a few spilled bytes cost less than the fifth
+// CTA's latency hiding gains on the loads); fp64: room for the pressure terms
+__global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 5 : 3)
     k_correct(Work w, UserPtrs p, int use_ws, int lo_valid, double s, int pmode, double cimp) {
     typedef typename A::V V;
     const int b = blockIdx.x + p.blk0;
