@@ -88,3 +88,17 @@ def test_spectral_z_rejected_where_it_does_not_apply():
         with pytest.raises(N.IBFError) as ei:
             Plan([g], precision=MIXED, tuning=[dict(yz_kernel=4)])
         assert ei.value.status in (N.IBF_ERR_INVALID_ARG, N.IBF_ERR_UNSUPPORTED_SIZE)
+
+
+def test_autotune_on_uniform_z_matches_oracle():
+    """The autotuner offers spectral z on a uniform grid; whatever it picks matches the oracle."""
+    g = Grid(64, 48, 32, 2 * math.pi, 1.5, 2.0, beta=0.0)
+    og = O.Grid(64, 48, 32, lx=g.lx, ly=g.ly, lz=g.lz, beta=0.0)
+    u, v, w = synth.uniform_velocity_np(64, 64, 48, 32)
+    phi_o = O.project(og, u, v, w, dt=2e-3, alpha=0.5)[0]
+    plan = Plan([g], precision=MIXED, refine_steps=1, autotune=True)
+    assert plan.tuning(0)["yz_kernel"] in (1, 2, 3, 4)
+    (uo, vo, wo, po) = plan.project(cuda(u), cuda(v), cuda(w), 2e-3, 0.5)
+    torch.cuda.synchronize()
+    plan.close()
+    assert rel_l2(po.cpu().numpy(), phi_o) <= TOL[MIXED]
