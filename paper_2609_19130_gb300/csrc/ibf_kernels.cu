@@ -553,10 +553,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
         phh = w.phi_hi + G.cell_off + base;
         phl = w.phi_lo + G.cell_off + base;
     }
-    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-        const int jl = (int)fdiv((unsigned)t, fnx), i = t - jl * nx;
-        const cx<T> z = buf[(jl >> 1) * sstride + pos_nat((W && G.wall_x) ? dct_perm(i, nx) : i, fN2)];
-        const T val = (jl & 1) ? z.y : z.x;
+    auto put = [&](int t, T val) {
         if constexpr (sizeof(T) == 8) {
             phi64[t] = (double)val;
         } else {
@@ -571,6 +568,27 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                 phl[t] = nw.lo;
             }
         }
+    };
+    if (!(W && G.wall_x) && (int)blockDim.x % N2 == 0) {
+        // rows outer; along a row the FFT position advances by blockDim + blockDim / N2
+        // per step (N2 divides the block size), so the inner loop needs no division
+        const int nrow = ncell / nx, pos0 = pos_nat(threadIdx.x, fN2);
+        const int pstep = (int)blockDim.x + (int)blockDim.x / N2;
+        for (int jl = 0; jl < nrow; ++jl) {
+            const cx<T> *seq = buf + (jl >> 1) * sstride;
+            const bool odd = (jl & 1) != 0;
+            int pos = pos0;
+            for (int i = threadIdx.x; i < nx; i += blockDim.x, pos += pstep) {
+                const cx<T> z = seq[pos];
+                put(jl * nx + i, odd ? z.y : z.x);
+            }
+        }
+        return;
+    }
+    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+        const int jl = (int)fdiv((unsigned)t, fnx), i = t - jl * nx;
+        const cx<T> z = buf[(jl >> 1) * sstride + pos_nat((W && G.wall_x) ? dct_perm(i, nx) : i, fN2)];
+        put(t, (jl & 1) ? z.y : z.x);
     }
 }
 
