@@ -47,10 +47,10 @@ BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of each
 # kernel from one ncu capture (512x512x128 mixed, see profiles/), valid while the
 # kernel sources hash to SOURCES_SHA256; otherwise the roofline's traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.70, "x_forward_residual": 15.26, "correct": 65.29,
-                          "yz_forward": 8.40, "yz_backward": 8.40, "x_inverse_store": 6.55,
-                          "x_inverse_accumulate": 6.56}
-NCU_SOURCES_SHA256 = "bd02136c8cf80c62555945e5d328cf35cff8084066e37982d665502b75aaf0d1"
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.70, "x_forward_residual": 15.25, "correct": 65.27,
+                          "yz_forward": 8.41, "yz_backward": 8.41, "x_inverse_store": 6.56,
+                          "x_inverse_accumulate": 6.57}
+NCU_SOURCES_SHA256 = "67799f697f70013cb4ae77c0ea8f8a738bc5c8771ed52c5c61669397877b6eab"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
                   "ibf_internal.h", "ibf_viscous.h")
 # the same for the viscous solve's kernels (mixed path)
