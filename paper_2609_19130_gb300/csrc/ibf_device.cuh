@@ -19,6 +19,16 @@ template <typename T> struct cx { T x, y; };
 
 template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+// fp32: one packed two-lane instruction (sm_100 family) per complex add or subtract,
+// each lane rounded exactly as the scalar operation (a - b as fma(b, -1, a))
+template <> __device__ __forceinline__ cx<float> cadd<float>(cx<float> a, cx<float> b) {
+    const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    return {r.x, r.y};
+}
+template <> __device__ __forceinline__ cx<float> csub<float>(cx<float> a, cx<float> b) {
+    const float2 r = __ffma2_rn(make_float2(b.x, b.y), make_float2(-1.f, -1.f), make_float2(a.x, a.y));
+    return {r.x, r.y};
+}
 template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }

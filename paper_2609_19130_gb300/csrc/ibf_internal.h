@@ -58,7 +58,7 @@ struct GridDev {
     long long cell_off;        // offset of the grid's per-cell workspace (cells)
     long long tab_off;         // offset of the grid's pivot table (entries)
     int z_off;                 // offset of the grid's per-level arrays ((nz+1) entries each)
-    int part_off;              // offset of the grid's partial sums (nz * nrb entries)
+    int part_off;              // offset of the grid's partial sums (nz * nrb entries, twice that with xfwd_split)
     int twx_off, twy_off;      // offsets of exp(-2 pi i r/N) tables for nx and ny (complex entries)
     int xblk_off, yzblk_off;   // first block of the grid in x-kernel / yz-kernel launches
     double dx, dy, rdx, rdy;   // spacings and their inverses
@@ -86,6 +86,7 @@ struct Work {
     int ngrids;
     int walls;                 // some grid has a wall-bounded x or y (selects the kernels that handle it)
     int xinv_split;            // mixed path, every grid's rows divisible by 4: half-block inverse x-FFT CTAs
+    int xfwd_split;            // the same condition: half-block forward x-FFT CTAs
     const int *xblk_start;     // prefix of x-kernel blocks over grids [ngrids+1]
     const int *yzblk_start;    // prefix of column blocks over all grids [ngrids+1] (pivot table)
     const int *ystr_start;     // prefix of column blocks over grids with streaming y/z kernels

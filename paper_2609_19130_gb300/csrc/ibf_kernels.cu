@@ -36,8 +36,11 @@ constexpr int kRowGroup = 4;  // rows whose loads are issued together (memory-le
 // Right-hand side of one solve for a block of rows of plane k, then the real FFT
 // along x of the rows (two rows per complex transform), stored as x-modes.
 // W: the launch contains wall-bounded grids (compiled out of periodic-only plans).
-template <typename T, class A, int MODE, bool W>
-__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
+// SPLIT = 2 (mixed path, rows divisible by 4): two CTAs of kXThreads / 2 threads per
+// row block, each forming and transforming half of its rows, so that one CTA's
+// transform overlaps another's loads; each half writes its own plane-sum slot.
+template <typename T, class A, int MODE, bool W, int SPLIT>
+__global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T) == 4 ? 2 : 1))
     k_xfwd(Work w, UserPtrs p, int use_ws, int lo_valid, double s, double rs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
@@ -45,13 +48,14 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     __shared__ float redf[kXThreads / 32];
     typedef typename A::V V;
 
-    const int b = blockIdx.x + p.blk0;
+    const int b = blockIdx.x / SPLIT + p.blk0;
+    const int half = SPLIT == 2 ? (int)(blockIdx.x & 1u) : 0;
     const int g = find_grid(w.xblk_start, w.ngrids, b);
     const GridDev &G = w.grids[g];
     const int lb = b - __ldg(w.xblk_start + g);
-    const int nrb = G.nrb, rows = G.rows;
+    const int nrb = G.nrb, rows = G.rows / SPLIT;
     const int k = lb / nrb, rb = lb - k * nrb;
-    const int j0 = rb * rows;
+    const int j0 = rb * G.rows + half * rows;
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     // sequences one complex element further apart than their length, so that the
     // split / gather steps, which read the same position of several sequences, do not
@@ -375,13 +379,14 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     // plane sums of this block's rows (for the singular mode), fixed reduction order:
     // of the right-hand side in the first pass; of phi in a refinement pass (k_00 forms
     // the plane means of the residual from both, since x and y differences sum to zero
-    // over a plane)
+    // over a plane).  With the split, a slot per half row block.
+    const int pslot = G.part_off + (k * nrb + rb) * SPLIT + half;
     if (DIVL || MODE == XM_ADJ) {
         V tot = Red<A>::sum(acc, red);
-        if (threadIdx.x == 0) w.partial[G.part_off + k * nrb + rb] = A::store(tot);
+        if (threadIdx.x == 0) w.partial[pslot] = A::store(tot);
     } else if (MODE != XM_COPY) {
         V totp = Red<A>::sum(acc_phi, red);
-        if (threadIdx.x == 0) w.partial_phi[G.part_off + k * nrb + rb] = A::store(totp);
+        if (threadIdx.x == 0) w.partial_phi[pslot] = A::store(totp);
     }
     if (DIVL) {
         float mx = block_max(vmax, redf);
@@ -396,12 +401,12 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 2 : 1)
     const int mb = G.mb, ncb = G.ncb, nxh = G.nxh;
     cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + (size_t)k * ncb * ny * mb;
     const int nout = ncb * rows * mb;
-    const FDiv fmb = G.fmb, frows = G.frows;
-    if (mb == 1 && kXThreads % rows == 0 && !wall_x) {
+    const FDiv fmb = G.fmb, frows = SPLIT == 2 ? G.fnpair : G.frows;  // fnpair: rows / 2
+    if (mb == 1 && (kXThreads / SPLIT) % rows == 0 && !wall_x) {
         // one x-mode per column block: every thread keeps one row jl and steps through
-        // the modes m0, m0 + kXThreads / rows, ... (the rows of one mode are contiguous
+        // the modes m0, m0 + blockDim / rows, ... (the rows of one mode are contiguous
         // in the spectrum, so consecutive threads store consecutive elements)
-        const int m0 = (int)fdiv((unsigned)threadIdx.x, frows), mstep = kXThreads / rows;
+        const int m0 = (int)fdiv((unsigned)threadIdx.x, frows), mstep = (kXThreads / SPLIT) / rows;
         const int jl = threadIdx.x - m0 * rows, j = j0 + jl;
         if (j < ny) {
             const cx<T> *seq = buf + (jl >> 1) * sstride;
@@ -806,36 +811,45 @@ __global__ void k_finalize(Work w, double *max_div, double *max_div_in, double *
 
 // ================================================================ launchers
 
+template <bool W, int SPLIT>
+cudaError_t launch_xfwd_mixed(int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
+                              double s, double rs, size_t smem, cudaStream_t st) {
+    const dim3 gr = grid1(SPLIT * nblk);
+    const int nt = kXThreads / SPLIT;
+    smem /= SPLIT;
+    if (mode == XM_DIV)
+        k_xfwd<float, DFArith, XM_DIV, W, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    else if (mode == XM_DIVQ)
+        k_xfwd<float, DFArith, XM_DIVQ, W, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    else if (mode == XM_RESID && !lo_valid)
+        k_xfwd<float, DFArith, XM_RESID0, W, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    else if (mode == XM_RESID)
+        k_xfwd<float, DFArith, XM_RESID, W, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    else if (mode == XM_COPY) {
+        if constexpr (W) return cudaErrorInvalidValue;  // periodic x and y only
+        else k_xfwd<float, DFArith, XM_COPY, false, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    } else
+        k_xfwd<float, DFArith, XM_ADJ, W, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    return cudaGetLastError();
+}
+
 template <bool W>
 cudaError_t launch_xfwd_w(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
                           double s, double rs, size_t smem, cudaStream_t st) {
-    if (mixed) {
-        if (mode == XM_DIV)
-            k_xfwd<float, DFArith, XM_DIV, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else if (mode == XM_DIVQ)
-            k_xfwd<float, DFArith, XM_DIVQ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else if (mode == XM_RESID && !lo_valid)
-            k_xfwd<float, DFArith, XM_RESID0, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else if (mode == XM_RESID)
-            k_xfwd<float, DFArith, XM_RESID, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else if (mode == XM_COPY) {
-            if constexpr (W) return cudaErrorInvalidValue;  // periodic x and y only
-            else k_xfwd<float, DFArith, XM_COPY, false><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        } else
-            k_xfwd<float, DFArith, XM_ADJ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-    } else {
-        if (mode == XM_DIV)
-            k_xfwd<double, F64Arith, XM_DIV, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else if (mode == XM_DIVQ)
-            k_xfwd<double, F64Arith, XM_DIVQ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else if (mode == XM_ADJ)
-            k_xfwd<double, F64Arith, XM_ADJ, W><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        else if (mode == XM_COPY) {
-            if constexpr (W) return cudaErrorInvalidValue;
-            else k_xfwd<double, F64Arith, XM_COPY, false><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-        } else
-            return cudaErrorInvalidValue;
-    }
+    if (mixed)
+        return w.xfwd_split ? launch_xfwd_mixed<W, 2>(mode, w, p, use_ws, lo_valid, nblk, s, rs, smem, st)
+                            : launch_xfwd_mixed<W, 1>(mode, w, p, use_ws, lo_valid, nblk, s, rs, smem, st);
+    if (mode == XM_DIV)
+        k_xfwd<double, F64Arith, XM_DIV, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    else if (mode == XM_DIVQ)
+        k_xfwd<double, F64Arith, XM_DIVQ, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    else if (mode == XM_ADJ)
+        k_xfwd<double, F64Arith, XM_ADJ, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    else if (mode == XM_COPY) {
+        if constexpr (W) return cudaErrorInvalidValue;
+        else k_xfwd<double, F64Arith, XM_COPY, false, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    } else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
@@ -936,26 +950,35 @@ cudaError_t set_smem_limits(int mixed) {
     auto set_all = [&](auto wtag) {
         constexpr bool W = decltype(wtag)::value;
         if (mixed) {
-            set((const void *)k_xfwd<float, DFArith, XM_DIV, W>);
-            set((const void *)k_xfwd<float, DFArith, XM_DIVQ, W>);
-            set((const void *)k_xfwd<float, DFArith, XM_RESID, W>);
-            set((const void *)k_xfwd<float, DFArith, XM_RESID0, W>);
-            set((const void *)k_xfwd<float, DFArith, XM_ADJ, W>);
+            set((const void *)k_xfwd<float, DFArith, XM_DIV, W, 1>);
+            set((const void *)k_xfwd<float, DFArith, XM_DIVQ, W, 1>);
+            set((const void *)k_xfwd<float, DFArith, XM_RESID, W, 1>);
+            set((const void *)k_xfwd<float, DFArith, XM_RESID0, W, 1>);
+            set((const void *)k_xfwd<float, DFArith, XM_ADJ, W, 1>);
+            set((const void *)k_xfwd<float, DFArith, XM_DIV, W, 2>);
+            set((const void *)k_xfwd<float, DFArith, XM_DIVQ, W, 2>);
+            set((const void *)k_xfwd<float, DFArith, XM_RESID, W, 2>);
+            set((const void *)k_xfwd<float, DFArith, XM_RESID0, W, 2>);
+            set((const void *)k_xfwd<float, DFArith, XM_ADJ, W, 2>);
             set((const void *)k_xinv<float, DFArith, IM_STORE, W, 1>);
             set((const void *)k_xinv<float, DFArith, IM_ACCUM, W, 1>);
             set((const void *)k_xinv<float, DFArith, IM_STORE, W, 2>);
             set((const void *)k_xinv<float, DFArith, IM_ACCUM, W, 2>);
         } else {
-            set((const void *)k_xfwd<double, F64Arith, XM_DIV, W>);
-            set((const void *)k_xfwd<double, F64Arith, XM_DIVQ, W>);
-            set((const void *)k_xfwd<double, F64Arith, XM_ADJ, W>);
+            set((const void *)k_xfwd<double, F64Arith, XM_DIV, W, 1>);
+            set((const void *)k_xfwd<double, F64Arith, XM_DIVQ, W, 1>);
+            set((const void *)k_xfwd<double, F64Arith, XM_ADJ, W, 1>);
             set((const void *)k_xinv<double, F64Arith, IM_STORE, W, 1>);
         }
     };
     set_all(std::false_type{});
     set_all(std::true_type{});
-    if (mixed) set((const void *)k_xfwd<float, DFArith, XM_COPY, false>);
-    else set((const void *)k_xfwd<double, F64Arith, XM_COPY, false>);
+    if (mixed) {
+        set((const void *)k_xfwd<float, DFArith, XM_COPY, false, 1>);
+        set((const void *)k_xfwd<float, DFArith, XM_COPY, false, 2>);
+    } else {
+        set((const void *)k_xfwd<double, F64Arith, XM_COPY, false, 1>);
+    }
     if (e == cudaSuccess) e = set_smem_limits_yz(mixed);
     return e;
 }

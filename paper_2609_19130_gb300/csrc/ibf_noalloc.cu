@@ -191,7 +191,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     const size_t o_spec = cv.take(csz * nspec), o_tab = cv.take(rsz * nspec);
     const size_t o_bdf = mixed ? cv.take(8 * cells) : 0;
     const size_t o_phh = mixed ? cv.take(4 * cells) : 0, o_phl = mixed ? cv.take(4 * cells) : 0;
-    const size_t npart = (size_t)nz * d.nrb;
+    const size_t npart = (size_t)nz * d.nrb;  // no half-block forward x-FFT CTAs here
     const size_t o_part = cv.take(8 * npart), o_partp = cv.take(8 * npart);
     const size_t o_mean = cv.take(8), o_maxb = cv.take(8), o_maxd = cv.take(8), o_err = cv.take(4);
     const size_t o_sol00 = cv.take(8 * L);

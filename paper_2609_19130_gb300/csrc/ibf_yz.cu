@@ -201,7 +201,7 @@ __device__ void yzbwd_pipe(const Work &w, const GridDev &G, int cb, unsigned cha
                     const float cp = c * t[q];
                     const cx<float> nx_ = state[q];
                     cx<float> ph = {d.x - cp * nx_.x, d.y - cp * nx_.y};
-                    if (cb == 0 && q == 0) ph = d;
+                    if (cb == 0 && q == 0) ph = {(float)w.sol00[G.z_off + k], 0.f};  // (0,0): k_00's solution
                     state[q] = ph;
                     buf[pos] = ph;
                 }
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 
             const T cp = c * tb[q];
             const cx<T> nx_ = state[q];
             cx<T> ph = {d.x - cp * nx_.x, d.y - cp * nx_.y};
-            if (cb == 0 && q == 0) ph = d;
+            if (cb == 0 && q == 0) ph = {(T)w.sol00[G.z_off + k], (T)0};  // (0,0): k_00's solution
             state[q] = ph;
             buf[mm * sstride + pos_nat(sn, fN2)] = ph;
         }
@@ -415,8 +415,9 @@ __device__ __forceinline__ double slab_lambda<double>(const GridDev &G, int m, i
     return -4.0 * G.rdx * G.rdx * sx * sx - 4.0 * G.rdy * G.rdy * sy * sy;
 }
 
+// fp32: capped at 128 registers, so that two CTAs fit on an SM where their slabs do
 template <typename T, bool W>
-__global__ void __launch_bounds__(kSlabThreads) k_yzslab(Work w) {
+__global__ void __launch_bounds__(kSlabThreads, sizeof(T) == 4 ? 2 : 1) k_yzslab(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = find_grid(w.slab_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
@@ -680,13 +681,16 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     double *rhs = sh00, *hz = sh00 + L;
     double *A0 = sh00 + 2 * L, *B0 = A0 + L, *C0 = B0 + L, *D0 = C0 + L;
     double *A1 = D0 + L, *B1 = A1 + L, *C1 = B1 + L, *D1 = C1 + L;
-    const double *part = w.partial + G.part_off;
+    const double *part = w.partial + G.part_off, *partp = w.partial_phi + G.part_off;
     double *Pk = A1;  // plane means of the phi being refined (A1 is free until the PCR steps)
     double loc = 0.0, locp = 0.0;
     bool bad = false;
+    // np slots per plane (one per row block, two with the half-block forward x-FFT CTAs),
+    // summed in order by one thread per plane (fp64 adds are scarce here: no shuffle tree)
+    const int np = nrb * (w.xfwd_split ? 2 : 1);
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         double S = 0.0;
-        for (int r = 0; r < nrb; ++r) S += part[k * nrb + r];
+        for (int r = 0; r < np; ++r) S += part[k * np + r];
         const double m = S * G.inv_nxy;  // plane mean of the first right-hand side b
         if (!isfinite(m)) bad = true;
         const double h = w.z.hz[zo + k];
@@ -694,7 +698,7 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
         hz[k] = h;
         if (!first_solve) {
             double P = 0.0;
-            for (int r = 0; r < nrb; ++r) P += w.partial_phi[G.part_off + k * nrb + r];
+            for (int r = 0; r < np; ++r) P += partp[k * np + r];
             Pk[k] = P * G.inv_nxy;
             locp += h * Pk[k];
         }
@@ -784,9 +788,10 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     const size_t stride = (size_t)G.ncb * G.ny * G.mb;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         const double v = rhs[k] - mphi;
-        // streaming and split paths: slot (0,0) of the y-transformed spectrum; the slab
-        // kernel (whose spectrum is still untransformed in y here) reads sol00
-        if (G.yzk != 1) spec[(size_t)k * stride] = {(T)v, (T)0};
+        // split and spectral-z paths: slot (0,0) of the y-transformed spectrum; the
+        // streaming backward kernel and the slab kernel read sol00 (so that on a plan of
+        // those two paths alone k_00 may run beside the forward kernel)
+        if (G.yzk >= 2) spec[(size_t)k * stride] = {(T)v, (T)0};
         w.sol00[zo + k] = v;
     }
 }
