@@ -151,6 +151,70 @@ __device__ __forceinline__ df df_resid4(df b, df c0, df c1, df d1, df c2, df d2,
     return two_sum(s.hi, lo);
 }
 
+// ------------------------------------------------------------------ float-float, two lanes
+// The sequences above on two independent values at once, in the packed fp32x2
+// instructions of the sm_100 family: every lane rounds exactly as the scalar operation
+// (a - b as fma(b, -1, a)), so each lane of a result equals the scalar result bit for bit.
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+struct df2 { float2 hi, lo; };
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+    const float2 s = p2add(a, b), bb = p2sub(s, a);
+    return {s, p2add(p2sub(a, p2sub(s, bb)), p2sub(b, bb))};
+}
+__device__ __forceinline__ df2 quick_two_sum2(float2 a, float2 b) {
+    const float2 s = p2add(a, b);
+    return {s, p2sub(b, p2sub(s, a))};
+}
+__device__ __forceinline__ df2 df_addf2(df2 a, float2 b) {
+    const df2 s = two_sum2(a.hi, b);
+    return quick_two_sum2(s.hi, p2add(s.lo, a.lo));
+}
+__device__ __forceinline__ df2 sum3u2(float2 a, float2 b, float2 c) {
+    const df2 s = two_sum2(a, b);
+    const df2 t = two_sum2(s.hi, c);
+    return {t.hi, p2add(t.lo, s.lo)};
+}
+// the leading float of c d negated (-p) and the FMA-collected error of p, as in df_resid4
+__device__ __forceinline__ void prod_neg(df c, float dh, float dl, float &pn, float &e) {
+    pn = __fmul_rn(-c.hi, dh);
+    e = __fmaf_rn(c.hi, dh, pn);
+    e = __fmaf_rn(c.hi, dl, e);
+    e = __fmaf_rn(c.lo, dh, e);
+}
+__device__ __forceinline__ void prod_pos(df c, float dh, float dl, float &p, float &e) {
+    p = __fmul_rn(c.hi, dh);
+    e = __fmaf_rn(c.hi, dh, -p);
+    e = __fmaf_rn(c.hi, dl, e);
+    e = __fmaf_rn(c.lo, dh, e);
+}
+// df_resid4 on two values: products per lane, every sum in two-lane operations
+__device__ __forceinline__ df2 df_resid4_2(df2 b, df c0, df c1, df2 d1, df c2, df2 d2, df c3, df2 d3, df c4,
+                                           df2 d4) {
+    float2 n1, n2, n3, p4, e1, e2, e3, e4;
+    prod_neg(c1, d1.hi.x, d1.lo.x, n1.x, e1.x);
+    prod_neg(c1, d1.hi.y, d1.lo.y, n1.y, e1.y);
+    prod_neg(c2, d2.hi.x, d2.lo.x, n2.x, e2.x);
+    prod_neg(c2, d2.hi.y, d2.lo.y, n2.y, e2.y);
+    prod_neg(c3, d3.hi.x, d3.lo.x, n3.x, e3.x);
+    prod_neg(c3, d3.hi.y, d3.lo.y, n3.y, e3.y);
+    prod_pos(c4, d4.hi.x, d4.lo.x, p4.x, e4.x);
+    prod_pos(c4, d4.hi.y, d4.lo.y, p4.y, e4.y);
+    df2 s = two_sum2(b.hi, make_float2(-c0.hi, -c0.hi));
+    float2 lo = p2add(p2sub(b.lo, make_float2(c0.lo, c0.lo)), s.lo);
+    s = two_sum2(s.hi, n1);
+    lo = p2add(lo, s.lo);
+    s = two_sum2(s.hi, n2);
+    lo = p2add(lo, s.lo);
+    s = two_sum2(s.hi, n3);
+    lo = p2add(lo, s.lo);
+    s = two_sum2(s.hi, p4);
+    lo = p2add(lo, s.lo);
+    lo = p2add(lo, p2sub(p2sub(e4, e1), p2add(e2, e3)));
+    return two_sum2(s.hi, lo);
+}
+
 // fp64 -> df32 without fp64 arithmetic.  hi takes the sign, the exponent and the
 // top 23 fraction bits (truncated); lo = x - hi is formed from the remaining 29
 // bits (rounded to 24 by the integer->float conversion), so hi + lo == x within

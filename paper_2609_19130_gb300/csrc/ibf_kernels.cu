@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
             const float2 *bd = w.bdf + G.cell_off + pbase;
             float Pm = 0.f, Pc = 0.f;
             bool have = false;
+            df2 acc2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of phi, per lane
             for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
                 float pn[kRowGroup], pkp[kRowGroup], pkm[kRowGroup], peu[kRowGroup], ped[kRowGroup];
                 float2 bdv[kRowGroup];
@@ -266,40 +267,66 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                     Pm = pm0;
                     Pc = pc0;
                 }
+                // two rows at a time: their stencil neighbours gathered as scalars, then the
+                // residual of both in two-lane float-float operations (bit for bit the
+                // scalar sequence); both rows' values go to one FFT slot (x: even row, y: odd)
 #pragma unroll
-                for (int q = 0; q < kRowGroup; ++q) {
-                    const int jl = jg + q, j = j0 + jl;
-                    if (jl >= sm.r1) break;
-                    T val = (T)0;
-                    if (j < ny) {
-                        float Pip = __shfl_down_sync(0xffffffffu, Pc, 1);
-                        if (own_up) Pip = peu[q];
-                        float Pim = __shfl_up_sync(0xffffffffu, Pc, 1);
-                        if (own_dn) Pim = ped[q];
-                        if (wall_x && ii + 1 == nx) Pip = Pc;
-                        if (wall_x && ii == 0) Pim = Pc;
-                        float Pjp = pn[q], Pjm = Pm;
-                        if (wall_y && j + 1 == ny) Pjp = Pc;
-                        if (wall_y && j == 0) Pjm = Pc;
+                for (int q = 0; q < kRowGroup; q += 2) {
+                    const int jl0 = jg + q;
+                    if (jl0 >= sm.r1) break;  // warp-uniform
+                    float xp[2], xm[2], yp[2], ym[2], zp[2], zm[2], pc[2];
+                    bool live[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = j0 + jl0 + h;
+                        live[h] = jl0 + h < sm.r1 && j < ny;
+                        const float P = Pc;
+                        float Pip = __shfl_down_sync(0xffffffffu, P, 1);
+                        if (own_up) Pip = peu[q + h];
+                        float Pim = __shfl_up_sync(0xffffffffu, P, 1);
+                        if (own_dn) Pim = ped[q + h];
+                        if (wall_x && ii + 1 == nx) Pip = P;
+                        if (wall_x && ii == 0) Pim = P;
+                        float Pjp = pn[q + h], Pjm = Pm;
+                        if (wall_y && j + 1 == ny) Pjp = P;
+                        if (wall_y && j == 0) Pjm = P;
+                        xp[h] = Pip; xm[h] = Pim; yp[h] = Pjp; ym[h] = Pjm; pc[h] = P;
                         // top: Neumann (difference zero) or Dirichlet outlet (phi = 0 on the face)
-                        const float Pkp = (k + 1 < nz) ? pkp[q] : (G.dir_top ? 0.f : Pc);
-                        const float Pkm = (k > 0) ? pkm[q] : Pc;
-                        const df d2x = sum3u(Pip, Pim, -2.f * Pc), d2y = sum3u(Pjp, Pjm, -2.f * Pc);
-                        const df dzp = two_sum(Pkp, -Pc), dzm = two_sum(Pc, -Pkm);
-                        if (act) {
-                            const df bv = df_resid4(df{bdv[q].x, bdv[q].y}, cp, cu, d2x, cv, d2y, cwp, dzp, cwm, dzm);
-                            acc_phi = df_addf(acc_phi, Pc);
-                            val = df_to_f(bv) * scale;
+                        zp[h] = (k + 1 < nz) ? pkp[q + h] : (G.dir_top ? 0.f : P);
+                        zm[h] = (k > 0) ? pkm[q + h] : P;
+                        if (live[h]) {
+                            Pm = P;
+                            Pc = pn[q + h];
+                            have = true;
+                        } else {
+                            have = false;
                         }
-                        Pm = Pc;
-                        Pc = pn[q];
-                        have = true;
-                    } else {
-                        have = false;
                     }
-                    if (act) *(reinterpret_cast<T *>(buf + (jl >> 1) * sstride + spos) + (jl & 1)) = val;
+                    const float2 PC = make_float2(pc[0], pc[1]);
+                    const float2 NPC = p2mul(PC, make_float2(-1.f, -1.f)), M2 = p2add(NPC, NPC);
+                    const df2 d2x = sum3u2(make_float2(xp[0], xp[1]), make_float2(xm[0], xm[1]), M2);
+                    const df2 d2y = sum3u2(make_float2(yp[0], yp[1]), make_float2(ym[0], ym[1]), M2);
+                    const df2 dzp = two_sum2(make_float2(zp[0], zp[1]), NPC);
+                    const df2 dzm = two_sum2(PC, p2mul(make_float2(zm[0], zm[1]), make_float2(-1.f, -1.f)));
+                    const df2 bv2 = {make_float2(bdv[q].x, bdv[q + 1].x), make_float2(bdv[q].y, bdv[q + 1].y)};
+                    const df2 r = df_resid4_2(bv2, cp, cu, d2x, cv, d2y, cwp, dzp, cwm, dzm);
+                    const float2 val = p2mul(p2add(r.hi, r.lo), make_float2(scale, scale));
+                    const bool u0 = act && live[0], u1 = act && live[1];
+                    acc2 = df_addf2(acc2, make_float2(u0 ? pc[0] : 0.f, u1 ? pc[1] : 0.f));
+                    if (act) {
+                        const float v0 = u0 ? val.x : 0.f, v1 = u1 ? val.y : 0.f;
+                        float *slot = reinterpret_cast<float *>(buf + (jl0 >> 1) * sstride + spos);
+                        if ((jl0 & 1) == 0 && jl0 + 1 < sm.r1) {
+                            *reinterpret_cast<float2 *>(slot) = make_float2(v0, v1);
+                        } else {
+                            slot[jl0 & 1] = v0;
+                            if (jl0 + 1 < sm.r1)
+                                *(reinterpret_cast<float *>(buf + ((jl0 + 1) >> 1) * sstride + spos) + ((jl0 + 1) & 1)) = v1;
+                        }
+                    }
                 }
             }
+            acc_phi = df_add(acc_phi, df_add(df{acc2.hi.x, acc2.lo.x}, df{acc2.hi.y, acc2.lo.y}));
         } else {
             PhiSrc<A> ph;
             if constexpr (sizeof(T) == 4) {
