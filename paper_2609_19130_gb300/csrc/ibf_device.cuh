@@ -189,6 +189,24 @@ __device__ __forceinline__ void prod_pos(df c, float dh, float dl, float &p, flo
     e = __fmaf_rn(c.hi, dl, e);
     e = __fmaf_rn(c.lo, dh, e);
 }
+__device__ __forceinline__ df2 df_add2(df2 a, df2 b) {
+    const df2 s = two_sum2(a.hi, b.hi);
+    return quick_two_sum2(s.hi, p2add(s.lo, p2add(a.lo, b.lo)));
+}
+// df_dot3 on two values: products per lane, every sum in two-lane operations
+__device__ __forceinline__ df2 df_dot3_2(df c1, df2 d1, df c2, df2 d2, df c3, df2 d3) {
+    float2 p1, p2, p3, e1, e2, e3;
+    prod_pos(c1, d1.hi.x, d1.lo.x, p1.x, e1.x);
+    prod_pos(c1, d1.hi.y, d1.lo.y, p1.y, e1.y);
+    prod_pos(c2, d2.hi.x, d2.lo.x, p2.x, e2.x);
+    prod_pos(c2, d2.hi.y, d2.lo.y, p2.y, e2.y);
+    prod_pos(c3, d3.hi.x, d3.lo.x, p3.x, e3.x);
+    prod_pos(c3, d3.hi.y, d3.lo.y, p3.y, e3.y);
+    const df2 s = two_sum2(p1, p2);
+    const df2 t = two_sum2(s.hi, p3);
+    const float2 lo = p2add(p2add(p2add(e1, e2), p2add(e3, s.lo)), t.lo);
+    return two_sum2(t.hi, lo);
+}
 // df_resid4 on two values: products per lane, every sum in two-lane operations
 __device__ __forceinline__ df2 df_resid4_2(df2 b, df c0, df c1, df2 d1, df c2, df2 d2, df c3, df2 d3, df c4,
                                            df2 d4) {

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
             V vcur = A::zero();
             double vcur64 = 0.0;  // float-float divergence: v of the current row, fp64
             bool have_v = false;
+            df2 acc2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // float-float divergence: plane sum, per lane
             for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
                 // load phase: every fp64 input of up to kRowGroup rows is requested first
                 double ru[kRowGroup], rue[kRowGroup], rvn[kRowGroup], rw0[kRowGroup], rw1[kRowGroup],
@@ -169,6 +170,66 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                     if constexpr (IsDF<A>::value && DIVL) vcur64 = rv0;
                     else vcur = A::load(rv0);
                 }
+                if constexpr (IsDF<A>::value && DIVL) {
+                // float-float divergence, two rows at a time: the three face differences of
+                // each row in fp64 (three DADD per cell, each rounded to 2^-53 of the
+                // difference), the coefficient products per row, every sum of both rows in
+                // two-lane operations (bit for bit the scalar sequence)
+#pragma unroll
+                for (int q = 0; q < kRowGroup; q += 2) {
+                    const int jl0 = jg + q;
+                    if (jl0 >= sm.r1) break;  // warp-uniform
+                    df d1[2], d2[2], d3[2], dq[2];
+                    bool live[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = j0 + jl0 + h;
+                        live[h] = jl0 + h < sm.r1 && j < ny;
+                        double Un = __shfl_down_sync(0xffffffffu, ru[q + h], 1);
+                        if (own_up) Un = rue[q + h];
+                        const double Vc = vcur64;
+                        d1[h] = f64_to_df(__dsub_rn(Un, ru[q + h]));
+                        d2[h] = f64_to_df(__dsub_rn(rvn[q + h], Vc));
+                        d3[h] = f64_to_df(__dsub_rn(rw1[q + h], rw0[q + h]));
+                        if (MODE == XM_DIVQ && pp) dq[h] = A::mul(cp, A::load(rp[q + h]));
+                        if (live[h]) {
+                            vcur64 = rvn[q + h];
+                            have_v = true;
+                        } else {
+                            have_v = false;
+                        }
+                    }
+                    df2 bv = df_dot3_2(cu, df2{make_float2(d1[0].hi, d1[1].hi), make_float2(d1[0].lo, d1[1].lo)},
+                                       cv, df2{make_float2(d2[0].hi, d2[1].hi), make_float2(d2[0].lo, d2[1].lo)},
+                                       cwp, df2{make_float2(d3[0].hi, d3[1].hi), make_float2(d3[0].lo, d3[1].lo)});
+                    if (MODE == XM_DIVQ && pp)
+                        bv = df_add2(bv, df2{make_float2(dq[0].hi, dq[1].hi), make_float2(dq[0].lo, dq[1].lo)});
+                    const bool u0 = act && live[0], u1 = act && live[1];
+                    const float2 val = p2mul(p2add(bv.hi, bv.lo), make_float2(scale, scale));
+                    if (u0) {
+                        vmax = fmaxf(vmax, fabsf(bv.hi.x));
+                        w.bdf[G.cell_off + pbase + (j0 + jl0) * nx + i] = make_float2(bv.hi.x, bv.lo.x);
+                    }
+                    if (u1) {
+                        vmax = fmaxf(vmax, fabsf(bv.hi.y));
+                        w.bdf[G.cell_off + pbase + (j0 + jl0 + 1) * nx + i] = make_float2(bv.hi.y, bv.lo.y);
+                    }
+                    const df2 z = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    acc2 = df_add2(acc2, df2{make_float2(u0 ? bv.hi.x : z.hi.x, u1 ? bv.hi.y : z.hi.y),
+                                             make_float2(u0 ? bv.lo.x : z.lo.x, u1 ? bv.lo.y : z.lo.y)});
+                    if (act) {
+                        const float v0 = u0 ? val.x : 0.f, v1 = u1 ? val.y : 0.f;
+                        float *slot = reinterpret_cast<float *>(buf + (jl0 >> 1) * sstride + spos);
+                        if ((jl0 & 1) == 0 && jl0 + 1 < sm.r1) {
+                            *reinterpret_cast<float2 *>(slot) = make_float2(v0, v1);
+                        } else {
+                            slot[jl0 & 1] = v0;
+                            if (jl0 + 1 < sm.r1)
+                                *(reinterpret_cast<float *>(buf + ((jl0 + 1) >> 1) * sstride + spos) + ((jl0 + 1) & 1)) = v1;
+                        }
+                    }
+                }
+                } else {
 #pragma unroll
                 for (int q = 0; q < kRowGroup; ++q) {
                     const int jl = jg + q, j = j0 + jl;
@@ -226,7 +287,10 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                     }
                     if (act) *(reinterpret_cast<T *>(buf + (jl >> 1) * sstride + spos) + (jl & 1)) = val;
                 }
+                }
             }
+            if constexpr (IsDF<A>::value && DIVL)
+                acc = df_add(acc, df_add(df{acc2.hi.x, acc2.lo.x}, df{acc2.hi.y, acc2.lo.y}));
         } else if constexpr (MODE == XM_RESID0 && IsDF<A>::value) {
             // first refinement sweep: phi_0 is plain fp32, so the second differences are
             // exact float sums (a missing wall neighbour is replaced by the cell itself,

@@ -179,6 +179,9 @@ __device__ void yzbwd_pipe(const Work &w, const GridDev &G, int cb, unsigned cha
         }
         cp_async_commit();
     };
+    // the (0,0) mode's solution (k_00) for slot 0 of block 0, loaded one plane ahead
+    const bool own00 = cb == 0 && tt == 0;
+    double s00n = own00 ? w.sol00[G.z_off + plane_of(0)] : 0.0;
     if (!fw) {
         for (int q = tt; q < ny; q += kPipeT) state[q] = {0.f, 0.f};
         issue(0);
@@ -195,13 +198,15 @@ __device__ void yzbwd_pipe(const Work &w, const GridDev &G, int cb, unsigned cha
                 cx<float> *buf = fb(it);
                 const float *t = tb(it);
                 const float c = cz[k];
+                const double s00 = s00n;
+                if (own00 && it + 1 < nz) s00n = w.sol00[G.z_off + plane_of(it + 1)];
                 for (int q = tt; q < ny; q += kPipeT) {
                     const int pos = pos_nat(q, fN2);
                     const cx<float> d = buf[pos];
                     const float cp = c * t[q];
                     const cx<float> nx_ = state[q];
                     cx<float> ph = {d.x - cp * nx_.x, d.y - cp * nx_.y};
-                    if (cb == 0 && q == 0) ph = {(float)w.sol00[G.z_off + k], 0.f};  // (0,0): k_00's solution
+                    if (cb == 0 && q == 0) ph = {(float)s00, 0.f};  // (0,0): k_00's solution
                     state[q] = ph;
                     buf[pos] = ph;
                 }
@@ -354,8 +359,13 @@ __global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 
 
     for (int q = tid; q < nslot; q += nthr) state[q] = {(T)0, (T)0};
     for (int s_ = 0; s_ < kYZStages - 1; ++s_) issue(nz - 1 - s_);
+    // the (0,0) mode's solution (k_00) for slot 0 of block 0, loaded one plane ahead
+    const bool own00 = cb == 0 && tid == 0;
+    double s00n = own00 ? w.sol00[G.z_off + nz - 1] : 0.0;
 
     for (int k = nz - 1; k >= 0; --k) {
+        const double s00 = s00n;
+        if (own00 && k > 0) s00n = w.sol00[G.z_off + k - 1];
         issue(k - (kYZStages - 1));
         cp_async_wait<kYZStages - 1>();
         __syncthreads();
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 
             const T cp = c * tb[q];
             const cx<T> nx_ = state[q];
             cx<T> ph = {d.x - cp * nx_.x, d.y - cp * nx_.y};
-            if (cb == 0 && q == 0) ph = {(T)w.sol00[G.z_off + k], (T)0};  // (0,0): k_00's solution
+            if (cb == 0 && q == 0) ph = {(T)s00, (T)0};  // (0,0): k_00's solution
             state[q] = ph;
             buf[mm * sstride + pos_nat(sn, fN2)] = ph;
         }
