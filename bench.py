@@ -47,14 +47,14 @@ BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of each
 # kernel from one ncu capture (512x512x128 mixed, see profiles/), valid while the
 # kernel sources hash to SOURCES_SHA256; otherwise the roofline's traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.70, "x_forward_residual": 15.25, "correct": 65.27,
-                          "yz_forward": 8.41, "yz_backward": 8.41, "x_inverse_store": 6.56,
-                          "x_inverse_accumulate": 6.57}
-NCU_SOURCES_SHA256 = "67799f697f70013cb4ae77c0ea8f8a738bc5c8771ed52c5c61669397877b6eab"
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.47, "x_forward_residual": 15.27, "correct": 65.24,
+                          "yz_forward": 8.41, "yz_backward": 8.41, "x_inverse_store": 6.55,
+                          "x_inverse_accumulate": 6.56}
+NCU_SOURCES_SHA256 = "be37990f0f6b8d07fe2b9d1a745f991b3e45841a3f375aa087ee58d8edf90a91"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
                   "ibf_internal.h", "ibf_viscous.h")
 # the same for the viscous solve's kernels (mixed path)
-NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.31}
+NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.32}
 
 
 def kernel_sources_sha256():

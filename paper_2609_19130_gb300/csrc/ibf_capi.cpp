@@ -91,11 +91,6 @@ struct ibf_plan {
     long long ws_bytes = 0;
     long long total_cells = 0;
     cudaStream_t last_stream = nullptr;
-    // k_00 beside the y/z forward kernel (plans of streaming and slab grids only): a
-    // second stream forked from and joined to the caller's stream around it
-    bool k00_async = false;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // profiling
     bool prof = false;
     std::vector<ProfRec> prof_pending;
@@ -145,11 +140,6 @@ void free_all(ibf_plan *pl) {
     pl->prof_pending.clear();
     for (auto e : pl->ev_pool) cudaEventDestroy(e);
     pl->ev_pool.clear();
-    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
-    if (pl->ev_join) cudaEventDestroy(pl->ev_join);
-    if (pl->side) cudaStreamDestroy(pl->side);
-    pl->ev_fork = pl->ev_join = nullptr;
-    pl->side = nullptr;
 }
 
 ibf_status validate(const ibf_grid *g, std::vector<double> &zf) {
@@ -477,15 +467,6 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     pl->nyzblk = yzblk;
     pl->nstrblk = strblk;
     pl->nslabblk = slabblk;
-    // k_00 beside the forward y/z kernel: on plans without split or spectral-z grids
-    // (whose kernels write the spectrum slot that k_00 fills for them)
-    if (strblk > 0 && yfftblk == 0 && zdctblk == 0) {
-        cudaError_t e = cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "mode00 stream");
-        pl->k00_async = true;
-    }
 
     // per-level arrays
     const int nzt = zoff;
@@ -728,18 +709,6 @@ ibf_status for_chunks(Ctx &c, const char *name, const ibf_fields *in, const ibf_
 ibf_status solve_core(Ctx &c, int first) {
     ibf_plan *pl = c.pl;
     const Work &w = pl->work;
-    // k_00 needs only the plane sums of the x kernel before it and writes only sol00 on
-    // these plans, so it runs on the side stream while the forward kernel runs
-    const bool async00 = pl->k00_async;
-    if (async00) {
-        cudaError_t e = cudaEventRecord(pl->ev_fork, c.st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
-        if (e != cudaSuccess) return cuda_fail(e, "fork of the mode00 stream");
-        Ctx cs{pl, pl->side};
-        IBF_TRY(timed(cs, "mode00", [&]() { return launch_k00(w, pl->mixed, first, pl->maxnz, pl->side); }));
-        e = cudaEventRecord(pl->ev_join, pl->side);
-        if (e != cudaSuccess) return cuda_fail(e, "join of the mode00 stream");
-    }
     if (pl->nstrblk > 0)
         IBF_TRY(timed(c, "yz_forward", [&]() { return launch_yzfwd(pl->mixed, w, pl->nstrblk, pl->yzsmem, c.st); }));
     if (pl->nyfftblk > 0) {
@@ -749,12 +718,7 @@ ibf_status solve_core(Ctx &c, int first) {
     }
     if (pl->nzdctblk > 0)  // spectral z: DCT along z, division, inverse DCT (before k_00 writes the (0,0) column)
         IBF_TRY(timed(c, "z_dct_solve", [&]() { return launch_zdct(pl->mixed, w, pl->nzdctblk, pl->zdctsmem, c.st); }));
-    if (async00) {
-        const cudaError_t e = cudaStreamWaitEvent(c.st, pl->ev_join, 0);
-        if (e != cudaSuccess) return cuda_fail(e, "join of the mode00 stream");
-    } else {
-        IBF_TRY(timed(c, "mode00", [&]() { return launch_k00(w, pl->mixed, first, pl->maxnz, c.st); }));
-    }
+    IBF_TRY(timed(c, "mode00", [&]() { return launch_k00(w, pl->mixed, first, pl->maxnz, c.st); }));
     if (pl->nstrblk > 0)
         IBF_TRY(timed(c, "yz_backward", [&]() { return launch_yzbwd(pl->mixed, w, pl->nstrblk, pl->yzsmem, c.st); }));
     if (pl->nyfftblk > 0) {

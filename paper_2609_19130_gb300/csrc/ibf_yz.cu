@@ -799,8 +799,7 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         const double v = rhs[k] - mphi;
         // split and spectral-z paths: slot (0,0) of the y-transformed spectrum; the
-        // streaming backward kernel and the slab kernel read sol00 (so that on a plan of
-        // those two paths alone k_00 may run beside the forward kernel)
+        // streaming backward kernel and the slab kernel read sol00
         if (G.yzk >= 2) spec[(size_t)k * stride] = {(T)v, (T)0};
         w.sol00[zo + k] = v;
     }
