@@ -94,7 +94,7 @@ __global__ void k_helm_table(Work w, double beta, double *tab, float *tabf, cons
 // work for every warp when the blocks are narrow.  The x-FFT scaled by 1/(nx ny), so the
 // unnormalised inverse transforms return the field.
 template <typename T>
-__global__ void __launch_bounds__(kYZThreads) k_yhelm(Work w, int g, int gb, const T *fxy) {
+__global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? 4 : 1) k_yhelm(Work w, int g, int gb, const T *fxy) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const GridDev &G = w.grids[g];
     const int ncb = G.ncb, ngrp = (ncb + gb - 1) / gb;

@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kSlabThreads, sizeof(T) == 4 ? 2 : 1) k_yzslab
 // y) and written back in place, in slot order (forward) or row order (inverse).
 // Every (plane, block) is independent, so the launch has nz*ncb blocks per grid.
 template <typename T, int DIR, bool W>
-__global__ void __launch_bounds__(kYZThreads) k_yfft(Work w) {
+__global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? 4 : 1) k_yfft(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = find_grid(w.yfft_start, w.ngrids, blockIdx.x);
     const GridDev &G = w.grids[g];
@@ -821,7 +821,7 @@ template <> __device__ __forceinline__ float sinpi_T<float>(float x) { return si
 template <> __device__ __forceinline__ double sinpi_T<double>(double x) { return sinpi(x); }
 
 template <typename T>
-__global__ void __launch_bounds__(kYZThreads) k_zdct(Work w) {
+__global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? 4 : 1) k_zdct(Work w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TM = zdct_lines<T>();
     const int g = find_grid(w.zdct_start, w.ngrids, blockIdx.x);
