@@ -66,6 +66,9 @@ VARIANTS = [
     dict(yz_kernel=2, mb=2, tri=3), dict(yz_kernel=2, mb=4, tri=0),   # tri 0: default (Thomas + table)
     dict(yz_kernel=2, mb=1, tri=99),                                   # replaced by full reduction below
     dict(rows=2), dict(rows=6), dict(x_n1=2, y_n1=2), dict(x_n1=4, y_n1=4),
+    # rows divisible by 4 take the half-block forward x-FFT CTAs on the mixed path; 4 and
+    # 12 give the narrow grids odd row chunks per warp (rows processed two at a time)
+    dict(rows=4), dict(rows=12),
     dict(yz_kernel=3, mb=1), dict(yz_kernel=3, mb=4), dict(yz_kernel=3, mb=2, y_n1=2),
 ]
 
