@@ -50,7 +50,7 @@ BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x
 NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.47, "x_forward_residual": 15.27, "correct": 65.24,
                           "yz_forward": 8.41, "yz_backward": 8.41, "x_inverse_store": 6.55,
                           "x_inverse_accumulate": 6.56}
-NCU_SOURCES_SHA256 = "1a7712899a6b414363da147d41ac8c5855642fd9876fa4d87739a6b1f8875cee"
+NCU_SOURCES_SHA256 = "6c9d23051839a39f939bcafe5eac12aa66e17e407f3d0a5e50361f0b40a8d247"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
                   "ibf_internal.h", "ibf_viscous.h")
 # the same for the viscous solve's kernels (mixed path)

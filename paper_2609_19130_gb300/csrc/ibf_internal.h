@@ -103,8 +103,8 @@ struct Work {
     double *phi_ws;            // per-cell fp64 phi of the adjoint solve / of a pressure update (fp64 path)
     double *bws;               // per-cell fp64 right-hand side (fp64 path with the implicit pressure update)
     float *phi_hi, *phi_lo;    // per-cell float-float phi being refined (mixed path)
-    double *partial;           // per (grid, k, row block) plane sums of the right-hand side
-    double *partial_phi;       // per (grid, k, row block) plane sums of the current phi (refinement)
+    double *partial;           // per (grid, k, row block, half with xfwd_split) plane sums of the right-hand side
+    double *partial_phi;       // the same of the current phi (refinement)
     double *mean_b;            // [ngrids] removed weighted mean of the first right-hand side
     unsigned long long *maxb;  // [ngrids] max |rhs| (double bits), for max|D u*|
     unsigned long long *maxdiv;// [ngrids] max |D u| of the output (double bits)
