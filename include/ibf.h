@@ -21,8 +21,8 @@
  * with an FFT of the same length between a reordering and pre/post twiddles
  * (Makhoul 1980), instead of the real FFT.
  *
- * Discretisation fixed by this library (the paper states only "staggered,
- * second-order centred"):
+ * Discretisation fixed by this library (the paper's Section "Fluid Mechanics" gives
+ * only the scheme's type, staggered, and its order, second-order centred):
  *   cells i < nx, j < ny, k < nz;  dx = lx/nx, dy = ly/ny;
  *   z faces zf[0..nz] with zf[0] = 0, zf[nz] = lz;  hz_k = zf[k+1]-zf[k];
  *   cell centres zc_k = (zf_k + zf_{k+1})/2;  gz_k = zc_k - zc_{k-1};
@@ -278,14 +278,21 @@ ibf_status ibf_profile_reset(ibf_plan *plan);
  * Projects one grid like ibf_project (same layouts, conventions, precisions and
  * results; no statistics).  `in` and `out` are single ibf_fields of DEVICE pointers
  * (out may alias in); stream is a cudaStream_t or NULL.  The pivot table is rebuilt
- * on every call.  Every call shares the one array and leaves its contents behind, so
+ * on every call.  The call's small tables (grid descriptor, z metrics, twiddles) reach
+ * the device as the arguments of copy-kernel launches on `stream`: no host memory is
+ * read after the call returns, and the call does not wait for work already queued on
+ * the stream.  Every call shares the one array and leaves its contents behind, so
  * calls that overlap on the GPU (other streams, other host threads) race and corrupt
  * each other: order them.  The first call on a device looks up the array's device
  * address and caches it; make that first call before any stream capture.
- * opts->pressure must be IBF_P_PHI.
- * Errors: INVALID_ARG, UNSUPPORTED_BC, UNSUPPORTED_SIZE (also when the workspace
- * of the grid does not fit in IBF_NOALLOC_SCRATCH_BYTES: about 2.5 million cells in
- * IBF_MIXED, 4.5 million in IBF_FP64), CUDA. */
+ * opts->pressure must be IBF_P_PHI.  Device-side conditions (a non-finite right-hand
+ * side, an incompatible right-hand side) are not reported by this entry point: there
+ * is no plan whose error word ibf_plan_sync_status could read.
+ * Errors (all found on the host before anything is enqueued): INVALID_ARG,
+ * UNSUPPORTED_BC, UNSUPPORTED_SIZE (also when the workspace of the grid does not fit
+ * in IBF_NOALLOC_SCRATCH_BYTES: about 2.5 million cells in IBF_MIXED, 4.5 million in
+ * IBF_FP64, or when a kernel's shared memory exceeds the limit ibf_projection_plan
+ * applies); CUDA when a CUDA call fails. */
 #define IBF_NOALLOC_SCRATCH_BYTES (64ull << 20)
 ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *opts, const ibf_fields *in,
                                const ibf_fields *out, double dt, double alpha, void *stream);

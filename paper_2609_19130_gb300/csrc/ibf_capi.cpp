@@ -142,7 +142,11 @@ void free_all(ibf_plan *pl) {
     pl->ev_pool.clear();
 }
 
-ibf_status validate(const ibf_grid *g, std::vector<double> &zf) {
+}  // namespace
+
+// Host validation of one grid descriptor; fills zf with the nz + 1 z faces (the
+// caller's, or the tanh map).  Shared by ibf_projection_plan and ibf_project_noalloc.
+ibf_status ibf::validate_grid(const ibf_grid *g, std::vector<double> &zf) {
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return IBF_ERR_INVALID_ARG;
     if (!(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0)) return IBF_ERR_INVALID_ARG;
     if (!std::isfinite(g->lx) || !std::isfinite(g->ly) || !std::isfinite(g->lz)) return IBF_ERR_INVALID_ARG;
@@ -176,6 +180,8 @@ ibf_status validate(const ibf_grid *g, std::vector<double> &zf) {
     zf[nz] = g->lz;
     return IBF_OK;
 }
+
+namespace {
 
 // magic numbers of FDiv (round-up method, valid for dividends below 2^31)
 FDiv make_fdiv(unsigned d) {
@@ -229,7 +235,7 @@ ibf_status upload(const void *host, void *dev, size_t bytes) {
 
 // dynamic shared memory a kernel may request (the opt-in maximum less a margin for the
 // kernels' static shared memory)
-size_t smem_cap(const cudaDeviceProp &prop) { return (size_t)prop.sharedMemPerBlockOptin - 1024; }
+size_t smem_cap(const cudaDeviceProp &prop) { return smem_cap_of(prop.sharedMemPerBlockOptin); }
 
 int ilog2_floor(int n) {
     int l = 0;
@@ -340,7 +346,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
     for (int g = 0; g < ngrids; ++g) {
         GridHost &H = pl->grids[g];
         H.g = grids[g];
-        IBF_TRY(validate(&grids[g], H.zf));
+        IBF_TRY(validate_grid(&grids[g], H.zf));
         H.g.zf = nullptr;
         GridDev &d = H.d;
         memset(&d, 0, sizeof(d));
@@ -863,7 +869,7 @@ float time_shape(TuneBench &b, const ibf_tuning &t) {
 
 ibf_status tune_grid(const ibf_grid &g, const ibf_opts &opts, int device, ibf_tuning *t) {
     std::vector<double> zf;
-    IBF_TRY(validate(&g, zf));
+    IBF_TRY(validate_grid(&g, zf));
     const bool zuni = z_uniform(zf);
     TuneKey key;
     const int kv[15] = {g.nx, g.ny, g.nz, g.bc_x, g.bc_y, g.bc_zhi, opts.precision, opts.refine_steps,
@@ -1011,7 +1017,7 @@ ibf_status ibf_projection_plan_tuned(ibf_plan **plan, const ibf_grid *grids, int
     // host-side validation of every grid before touching the device
     for (int g = 0; g < ngrids; ++g) {
         std::vector<double> zf;
-        ibf_status s = validate(&grids[g], zf);
+        ibf_status s = validate_grid(&grids[g], zf);
         if (s != IBF_OK) return s;
         if (tuning) {
             const ibf_tuning &t = tuning[g];

@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "../../include/ibf.h"
+
 namespace ibf {
 
 // Largest number of grids whose user pointers travel in one launch's parameters.
@@ -149,5 +153,12 @@ cudaError_t launch_build_table(int mixed, const Work &w, int nblk, cudaStream_t 
 cudaError_t set_smem_limits(int mixed);
 cudaError_t set_smem_limits_yz(int mixed);  // the y/z kernels' share of set_smem_limits
 cudaError_t set_smem_cap(const void *fn);   // one kernel's dynamic shared-memory cap
+
+// Host side (ibf_capi.cpp), shared by the plan and the no-allocation entry point.
+// Validates one grid descriptor and fills zf with its nz + 1 z faces.
+ibf_status validate_grid(const ibf_grid *g, std::vector<double> &zf);
+// Dynamic shared memory a plan lets one kernel request: the device's opt-in maximum
+// per block less a margin for the kernels' static shared memory.
+inline size_t smem_cap_of(int optin_bytes) { return (size_t)optin_bytes - 1024; }
 
 }  // namespace ibf

@@ -16,6 +16,11 @@
 // (cudaGetSymbolAddress) and caches it; that first call should come before any
 // stream capture.  Grids whose workspace does not fit are rejected with
 // IBF_ERR_UNSUPPORTED_SIZE before anything is launched.
+//
+// The small per-call tables (grid descriptor, z metrics, twiddles) are built on the
+// host and reach the array as the by-value arguments of a copy kernel, in chunks: the
+// launch copies the arguments, so no host buffer is read after the call returns and
+// no copy from pageable memory waits on the stream.
 #include "../../include/ibf.h"
 
 #include <cuda_runtime.h>
@@ -93,6 +98,17 @@ struct Carve {
     }
 };
 
+// Host-to-device transfer of the per-call tables through kernel arguments: one launch
+// per chunk of up to kPutBytes (the chunk travels in the launch's parameter block, which
+// sm_70 and newer accept up to 32764 bytes).
+constexpr unsigned kPutBytes = 16384;
+struct PutChunk {
+    uint4 v[kPutBytes / 16];
+};
+__global__ void __launch_bounds__(256) k_put_chunk(uint4 *dst, unsigned n16, const PutChunk c) {
+    for (unsigned i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = c.v[i];
+}
+
 }  // namespace
 
 extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *opts, const ibf_fields *in,
@@ -105,7 +121,13 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     if (opts->refine_steps < 0 || opts->refine_steps > 8 || opts->pressure != IBF_P_PHI) return IBF_ERR_INVALID_ARG;
     if (opts->precision == IBF_FP64 && opts->refine_steps != 0) return IBF_ERR_INVALID_ARG;
     const ibf_grid &g = *grid;
-    if (g.nx < 1 || g.ny < 1 || g.nz < 1 || !(g.lx > 0) || !(g.ly > 0) || !(g.lz > 0)) return IBF_ERR_INVALID_ARG;
+    // the checks of ibf_projection_plan (sizes, lengths, faces or tanh factor, boundary
+    // conditions), then the restrictions of this entry point
+    std::vector<double> zf;
+    {
+        const ibf_status vs = validate_grid(grid, zf);
+        if (vs != IBF_OK) return vs;
+    }
     if (g.bc_x != IBF_BC_PERIODIC || g.bc_y != IBF_BC_PERIODIC || g.bc_zlo != IBF_BC_NEUMANN ||
         g.bc_zhi != IBF_BC_NEUMANN)
         return IBF_ERR_UNSUPPORTED_BC;
@@ -115,27 +137,13 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     const int mixed = opts->precision == IBF_MIXED;
     const int nz = g.nz;
 
-    // z faces: caller's array or the tanh map
-    std::vector<double> zf(nz + 1);
-    if (g.zf) {
-        for (int k = 0; k <= nz; ++k) zf[k] = g.zf[k];
-        if (std::fabs(zf[0]) > 1e-12 * g.lz || std::fabs(zf[nz] - g.lz) > 1e-12 * g.lz) return IBF_ERR_INVALID_ARG;
-    } else {
-        if (!(g.beta >= 0) || !std::isfinite(g.beta)) return IBF_ERR_INVALID_ARG;
-        for (int k = 0; k <= nz; ++k)
-            zf[k] = (g.beta == 0.0) ? g.lz * (double)k / nz
-                                    : 0.5 * g.lz * (1.0 + std::tanh(g.beta * (2.0 * k / nz - 1.0)) / std::tanh(g.beta));
+    int dev = 0, nsm = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return IBF_ERR_CUDA;
     }
-    zf[0] = 0.0;
-    zf[nz] = g.lz;
-    for (int k = 0; k < nz; ++k)
-        if (!(zf[k + 1] > zf[k])) return IBF_ERR_INVALID_ARG;
-
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return IBF_ERR_CUDA;
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return IBF_ERR_CUDA;
-    const int nsm = prop.multiProcessorCount;
     const size_t csz = mixed ? 8 : 16, rsz = mixed ? 4 : 8;
 
     // launch shapes: the rules of ibf_projection_plan for a one-grid plan
@@ -173,9 +181,8 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
         if (mixed && d.mb == 1 && !d.wall_y) yzsmem = std::max(yzsmem, yz_pipe_smem(d.ny, (int)sstr));
     }
     const size_t smem00 = (size_t)10 * (nz + 1) * 8;
-    if (xsmem > (size_t)prop.sharedMemPerBlockOptin || yzsmem > (size_t)prop.sharedMemPerBlockOptin ||
-        smem00 > (size_t)prop.sharedMemPerBlockOptin)
-        return IBF_ERR_UNSUPPORTED_SIZE;
+    const size_t cap = smem_cap_of(optin);  // the limit ibf_projection_plan applies
+    if (xsmem > cap || yzsmem > cap || smem00 > cap) return IBF_ERR_UNSUPPORTED_SIZE;
 
     // layout inside the scratch array: first the small tables uploaded from the host
     // (one copy), then the workspace written by the kernels
@@ -252,8 +259,14 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     tw(o_twy, d.ny, d.ny1);
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // pageable source: the copy is staged before cudaMemcpyAsync returns
-    if (cudaMemcpyAsync(base, img.data(), upload_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return IBF_ERR_CUDA;
+    // the tables, chunk by chunk, as kernel arguments (upload_bytes is a multiple of 256)
+    for (size_t o = 0; o < upload_bytes; o += kPutBytes) {
+        const size_t n = std::min<size_t>(kPutBytes, upload_bytes - o);
+        PutChunk c;
+        memcpy(c.v, img.data() + o, n);
+        k_put_chunk<<<1, 256, 0, st>>>(reinterpret_cast<uint4 *>(base + o), (unsigned)(n / 16), c);
+        if (cudaGetLastError() != cudaSuccess) return IBF_ERR_CUDA;
+    }
     if (cudaMemsetAsync(base + o_err, 0, 4, st) != cudaSuccess) return IBF_ERR_CUDA;
 
     Work w;

@@ -125,3 +125,29 @@ def test_tuning_validation_on_host(lib, bad, beta):
     o = N.ibf_opts(1, 1, 0, 0, 0.0)
     assert N.lib().ibf_projection_plan_tuned(C.byref(h), g, 1, C.byref(o), 0, t) == N.IBF_ERR_INVALID_ARG
     assert not h.value
+
+
+@pytest.mark.parametrize("kw,okw,expect", [
+    (dict(lx=float("inf")), {}, N.IBF_ERR_INVALID_ARG),      # rdx would be 0
+    (dict(lz=float("nan")), {}, N.IBF_ERR_INVALID_ARG),
+    (dict(nx=5), {}, N.IBF_ERR_UNSUPPORTED_SIZE),
+    (dict(nx=1 << 10, ny=1 << 10, nz=1 << 15), {}, N.IBF_ERR_UNSUPPORTED_SIZE),  # above 2^34 cells
+    (dict(bc_x=1), {}, N.IBF_ERR_UNSUPPORTED_BC),            # walls in x: not on this entry point
+    (dict(bc_zhi=2), {}, N.IBF_ERR_UNSUPPORTED_BC),          # outlet: not on this entry point
+    (dict(beta=float("inf")), {}, N.IBF_ERR_INVALID_ARG),
+    ({}, dict(pressure=1), N.IBF_ERR_INVALID_ARG),
+    ({}, dict(precision=0, refine_steps=1), N.IBF_ERR_INVALID_ARG),
+])
+def test_noalloc_validation_on_host(lib, kw, okw, expect):
+    """ibf_project_noalloc applies the plan's grid checks and its own restrictions on the
+    host, before any CUDA call (the device pointers below are never dereferenced)."""
+    g = dict(nx=16, ny=16, nz=8, lx=1.0, ly=1.0, lz=1.0, zf=None, beta=0.0,
+             bc_x=0, bc_y=0, bc_zlo=1, bc_zhi=1)
+    g.update(kw)
+    o = dict(precision=1, refine_steps=1, autotune=0, pressure=0, inv_re=0.0)
+    o.update(okw)
+    fake = C.c_void_p(0x1000)
+    f = N.ibf_fields(fake, fake, fake, fake)
+    st = N.lib().ibf_project_noalloc(C.byref(N.ibf_grid(**g)), C.byref(N.ibf_opts(**o)), C.byref(f),
+                                     C.byref(f), 1e-3, 1.0, None)
+    assert st == expect

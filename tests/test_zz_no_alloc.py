@@ -3,7 +3,8 @@
 It takes its workspace from one fixed device array instead of allocating it; its
 results must match the allocating entry point (ibf_project through a plan) on two
 calls in a row, with a different grid and precision on the second call, within the
-tolerances the parity tests use.  This file is collected last on purpose."""
+tolerances the parity tests use, and the FP64 oracle on one grid in both precisions.
+This file is collected last on purpose."""
 import ctypes as C
 import math
 
@@ -12,6 +13,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import oracle as O  # noqa: E402
 from paper_2609_19130_gb300 import FP64, MIXED, Grid, Plan, synth  # noqa: E402
 from paper_2609_19130_gb300 import _native as N  # noqa: E402
 
@@ -62,3 +64,24 @@ def test_noalloc_rejects_grids_beyond_its_array():
     w = torch.zeros(1, dtype=torch.float64, device="cuda")
     st, _ = noalloc(grid, MIXED, 1, u, v, w)
     assert st == N.IBF_ERR_UNSUPPORTED_SIZE
+
+
+@pytest.mark.parametrize("prec,refine,tol,utol", [(MIXED, 1, 1e-9, 1e-9), (FP64, 0, 1e-12, 1e-11)])
+def test_noalloc_matches_oracle(prec, refine, tol, utol):
+    """One stretched grid (96 = 12 x 8 along x, 48 = 8 x 6 along y, 36 levels) against the
+    FP64 oracle, with the parity tests' tolerances: phi in relative L2, the velocity in
+    max error relative to max|u*|."""
+    nx, ny, nz = 96, 48, 36
+    grid = Grid(nx, ny, nz, 2 * math.pi, 1.3, 2.0, beta=2.5)
+    hu, hv, hw = synth.uniform_velocity_np(41, nx, ny, nz)
+    u, v, w = (torch.from_numpy(a).cuda() for a in (hu, hv, hw))
+    st, got = noalloc(grid, prec, refine, u, v, w)
+    assert st == N.IBF_OK, N.status_string(st)
+    torch.cuda.synchronize()
+    og = O.Grid(nx, ny, nz, lx=grid.lx, ly=grid.ly, lz=2.0, beta=2.5)
+    phi, uo, vo, wo, _ = O.project(og, hu, hv, hw, dt=1e-3)
+    gp = got[3].cpu().numpy()
+    assert np.linalg.norm(gp - phi) / np.linalg.norm(phi) <= tol
+    umax = max(np.abs(a).max() for a in (hu, hv, hw))
+    for a, b in zip(got[:3], (uo, vo, wo)):
+        assert np.abs(a.cpu().numpy() - b).max() <= utol * umax
