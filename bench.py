@@ -44,6 +44,41 @@ BYTES_MIXED = {"x_forward_div": 36.0, "yz_forward": 10.0, "yz_backward": 10.0, "
                "x_forward_residual": 16.0, "x_inverse_accumulate": 16.0, "correct": 64.0, "mode00": 0.0}
 BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x_inverse_store": 16.0,
               "correct": 56.0, "mode00": 0.0}
+# fp64 path: its transforms and sweeps keep the fp64 pipe busy, so its roofline is that
+# pipe's rate (measured by libibf_probe.so) against algorithmic flops per cell: a complex
+# FFT of length N counted as 5 N log2 N flops (a real one of N as 2.5 N log2 N), so the
+# x transform of a real row costs 2.5 log2(nx) per cell and the y transform of the
+# nx/2 + 1 complex columns 5 log2(ny) (nx/2 + 1)/nx per cell; the divergence 8 flops and
+# its plane sum 1; a forward Thomas step per complex mode value 6 (r - a d: two FMAs,
+# times the pivot: two products), a backward step 4; the correction 12 (three
+# differences, three scalings, three FMAs).
+def fp64_flops_per_cell(nx, ny):
+    lx, ly = math.log2(nx), math.log2(ny)
+    cy = (nx // 2 + 1) / nx  # complex y-columns per cell
+    return {"x_forward_div": 9.0 + 2.5 * lx, "yz_forward": cy * (5.0 * ly + 6.0),
+            "yz_backward": cy * (5.0 * ly + 4.0), "x_inverse_store": 2.5 * lx, "correct": 12.0,
+            "mode00": 0.0}
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense fp64, NVIDIA's figure
+
+
+def fp64_peak():
+    """(TFLOP/s, kind, fp64 add Gop/s or None): the fp64 FMA rate of this device measured by
+    libibf_probe.so (two flops per FMA), else the nominal figure."""
+    import ctypes
+    try:
+        from paper_2609_19130_gb300 import build as B
+        lib = ctypes.CDLL(B.PROBE_LIB)
+        f, a = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        lib.ibfprobe_fp64_rates.argtypes = [ctypes.POINTER(ctypes.c_double)] * 2
+        if lib.ibfprobe_fp64_rates(ctypes.byref(f), ctypes.byref(a)) == 0 and f.value > 0:
+            return 2.0 * f.value / 1e3, "measured (fp64 FMA chains, libibf_probe.so)", a.value
+    except OSError:
+        pass
+    return FP64_NOMINAL_TFLOPS, "nominal", None
+
+
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of each
 # kernel from one ncu capture (512x512x128 mixed, see profiles/), valid while the
 # kernel sources hash to SOURCES_SHA256; otherwise the roofline's traffic is null.
@@ -163,6 +198,57 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
+def chunked_copy(dst, src, chunk_bytes):
+    """dst.copy_(src) as one asynchronous copy, or as copies of chunk_bytes each."""
+    if not chunk_bytes or dst.numel() * dst.element_size() <= chunk_bytes:
+        dst.copy_(src, non_blocking=True)
+        return
+    n = max(1, chunk_bytes // dst.element_size())
+    d, s_ = dst.view(-1), src.view(-1)
+    for a in range(0, d.numel(), n):
+        d[a:a + n].copy_(s_[a:a + n], non_blocking=True)
+
+
+def host_link_rates(h_up, h_down, d_up, d_down):
+    """Pinned host <-> device copy rates in GB/s: one field up alone, one down alone, and
+    both at once on two streams (CUDA events; best of three)."""
+    import torch
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nb_up, nb_down = h_up.numel() * 8, h_down.numel() * 8
+
+    def timed(fn):
+        best = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s1.wait_event(e0)
+            s2.wait_event(e0)
+            fn()
+            torch.cuda.current_stream().wait_stream(s1)
+            torch.cuda.current_stream().wait_stream(s2)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            best = t if best is None else min(best, t)
+        return best
+
+    def up():
+        with torch.cuda.stream(s1):
+            d_up.copy_(h_up, non_blocking=True)
+
+    def down():
+        with torch.cuda.stream(s2):
+            h_down.copy_(d_down, non_blocking=True)
+
+    def both():
+        up()
+        down()
+
+    return {"h2d_gbs": nb_up / timed(up) / 1e9, "d2h_gbs": nb_down / timed(down) / 1e9,
+            "both_gbs": (nb_up + nb_down) / timed(both) / 1e9, "bytes_each": [nb_up, nb_down]}
+
+
 def time_steps(plan, ins, outs, K, W, ws, flush=None):
     """W warm-up then K timed projections; returns ms per step (CUDA events, max over ranks)
     and the per-kernel profile over the timed steps.  With `flush` (a buffer larger than
@@ -274,26 +360,38 @@ def workload_config(nx, ny, nz, refine, zbeta=BETA):
             "grid": [nx, ny, nz], "refine_steps": refine}
 
 
-def cpu_baseline_child(spec: str):
-    """Runs in a fresh process: the FP64 oracle on an nx x ny x nz_sample slab of the workload."""
+def cpu_baseline_child(spec: str, reps: int = 1):
+    """Runs in a fresh process: the FP64 oracle on an nx x ny x nz_sample slab of the workload,
+    `reps` times on the same inputs; prints the seconds of each run."""
     from oracle import oracle as O
     from paper_2609_19130_gb300 import synth
     nx, ny, nz_sample = (int(x) for x in spec.split("x"))
     g = O.Grid(nx, ny, nz_sample, lx=LX, ly=LY, lz=LZ, beta=BETA)
     u, v, w = synth.uniform_velocity_np(SEED, nx, ny, nz_sample)
     O.lib()
-    t0 = time.perf_counter()
-    O.project(g, u, v, w, dt=DT)
-    dt = time.perf_counter() - t0
-    print(json.dumps({"seconds": dt, "cells": nx * ny * nz_sample, "cores": os.cpu_count()}))
+    secs = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.project(g, u, v, w, dt=DT)
+        secs.append(time.perf_counter() - t0)
+    print(json.dumps({"seconds": secs[-1], "all_seconds": secs, "cells": nx * ny * nz_sample,
+                      "cores": os.cpu_count()}))
 
 
-def run_cpu_baseline(nx: int, ny: int, nz_sample: int):
+def host_sample_nz(requested, nz):
+    """z levels of an oracle sample: the oracle's transforms run one plane per thread, so
+    the sample is rounded up to a multiple of the host's cores (at most nz)."""
+    c = os.cpu_count() or 1
+    return min(nz, max(c, ((requested + c - 1) // c) * c))
+
+
+def run_cpu_baseline(nx: int, ny: int, nz_sample: int, reps: int = 1):
     env = dict(os.environ)
     env["OMP_NUM_THREADS"] = str(os.cpu_count())
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", f"{nx}x{ny}x{nz_sample}"],
-                       capture_output=True, text=True, env=env, timeout=900)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", f"{nx}x{ny}x{nz_sample}",
+                        "--cpu-reps", str(reps)],
+                       capture_output=True, text=True, env=env, timeout=900 + 120 * reps)
     line = [l for l in r.stdout.splitlines() if l.startswith("{")]
     if r.returncode != 0 or not line:
         return None, r.stderr[-2000:]
@@ -307,17 +405,13 @@ def reference_arm(args):
     if rank != 0:
         return 0
     nx, ny, nz = (int(x) for x in args.size.split("x"))
-    nz_sample = min(args.ref_nz, nz)
-    times = []
-    cores = None
-    for i in range(args.warmup + args.steps):
-        res, err = run_cpu_baseline(nx, ny, nz_sample)
-        if res is None:
-            print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + (err or "")[-200:]}))
-            return 0
-        cores = res["cores"]
-        if i >= args.warmup:
-            times.append(res["seconds"])
+    nz_sample = host_sample_nz(args.ref_nz, nz)
+    res, err = run_cpu_baseline(nx, ny, nz_sample, reps=args.warmup + args.steps)
+    if res is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + (err or "")[-200:]}))
+        return 0
+    cores = res["cores"]
+    times = res["all_seconds"][args.warmup:]
     cells = nx * ny * nz_sample
     sec = sum(times) / len(times)
     value = cells / sec
@@ -340,17 +434,14 @@ def shard(n, ws, rank):
     return list(range(rank, n, ws))
 
 
-def bench_batch64(args):
-    """The batched workload: 64 uneven grids (nx, ny in {64,96,128,192}, nz in {64,128,256},
-    tanh beta in U[1,3], splitmix64 seed 1) projected by one plan, launch shapes autotuned;
-    one JSON line (not the headline, which is the single large grid).  Under torchrun the
-    grids are dealt across the ranks (independent problems: no collective on the data path)."""
+def measure_batch64(args, ws, rank, dev, autotune=True):
+    """The batched workload (config 3): 64 uneven grids (nx, ny in {64,96,128,192}, nz in
+    {64,128,256}, tanh beta in U[1,3], splitmix64 seed 1; velocity U[-1,1] of seed 1000+g)
+    projected by one plan whose launch shapes are autotuned per grid shape, one ibf_project
+    call per step.  Under torchrun the grids are dealt across the ranks (independent
+    problems: no collective on the data path).  Returns the measurement as a dict."""
     import torch
-    ws, rank, _ = dist_init()
     from paper_2609_19130_gb300 import MIXED, Grid, Plan, synth
-    from paper_2609_19130_gb300 import build as B
-    B.build()
-    dev = torch.device("cuda", torch.cuda.current_device())
     draws = synth.batch_grid_draws(1, 64)
     mine = shard(len(draws), ws, rank)
     all_cells = sum(nx * ny * nz for nx, ny, nz, _ in draws)
@@ -362,39 +453,62 @@ def bench_batch64(args):
         outs.append((torch.empty_like(u), torch.empty_like(v), torch.empty_like(w),
                      torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device=dev)))
     cells = sum(g.cells for g in grids)
-    plan = Plan(grids, precision=MIXED, refine_steps=args.refine, autotune=bool(args.autotune))
-    for _ in range(args.warmup):
+    t0 = time.perf_counter()
+    plan = Plan(grids, precision=MIXED, refine_steps=args.refine, autotune=bool(autotune))
+    plan_s = time.perf_counter() - t0
+    for _ in range(max(3, args.warmup)):
         plan.project_into(ins, outs, DT, 1.0)
+    plan.profile(True)
+    plan.profile_read(reset=True)
     torch.cuda.synchronize()
     barrier(ws)
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(args.steps, 10)
     with Clocks(dev.index) as ck:
         e0.record(st)
-        for _ in range(args.steps):
+        for _ in range(steps):
             plan.project_into(ins, outs, DT, 1.0)
         e1.record(st)
         torch.cuda.synchronize()
     barrier(ws)
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, ws)
+    prof = plan.profile_read(reset=True)
+    plan.profile(False)
     kinds = {}
     for gi in range(len(grids)):
         t = plan.tuning(gi)
         key = {1: "streaming", 2: "slab", 3: "split", 4: "spectral_z"}[t["yz_kernel"]]
         kinds[key] = kinds.get(key, 0) + 1
     plan.close()
-    if rank != 0:
-        return 0
-    print(json.dumps({
+    launches = int(sum(c for c, _ in prof.values()))
+    return {
         "metric": "cells/s per batched pressure projection (64 uneven grids)", "value": all_cells / (ms * 1e-3),
-        "unit": "cells/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "strong", "dtype": "f32", "data": "synthetic",
+        "unit": "cells/s", "ms_per_step": ms, "steps": steps, "scaling": "strong",
+        "hbm_frac_180B": 180.0 * all_cells / (ms * 1e-3) / 1e9 / peaks()[0],
         "config": {"workload": "64 grids, nx,ny in {64,96,128,192}, nz in {64,128,256}, beta U[1,3] (seed 1), "
-                               "U[-1,1] velocity (seed 1000+g)", "cells": all_cells, "refine_steps": args.refine,
+                               "U[-1,1] velocity (seed 1000+g), mixed, "
+                               f"{args.refine} refinement sweep(s)", "cells": all_cells,
                    "parallelism": f"grids dealt round-robin over {ws} rank(s)",
-                   "autotuned": bool(args.autotune), "yz_kernels": kinds,
+                   "autotuned": bool(autotune), "plan_seconds": plan_s, "yz_kernels": kinds,
                    "l2_policy": f"batch fields {cells * 56 / 1e9:.1f} GB > 129 MB L2: no flush"},
-        "clocks": ck.summary()}))
+        "kernels": {k: {"launches": c, "ms_per_launch": t / c, "share": t / sum(x[1] for x in prof.values())}
+                    for k, (c, t) in prof.items()},
+        "launches_per_step": launches / steps, "gpu_launches": launches,
+        "clocks": ck.summary()}
+
+
+def bench_batch64(args):
+    """--batch64: the batched workload alone, as its own JSON line."""
+    import torch
+    ws, rank, _ = dist_init()
+    from paper_2609_19130_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    r = measure_batch64(args, ws, rank, dev, autotune=bool(args.autotune) or not args.no_autotune_batch)
+    if rank == 0:
+        line = dict(r, n_gpus=ws, warmup=args.warmup, higher_is_better=True, dtype="f32", data="synthetic")
+        print(json.dumps(line))
     return 0
 
 
@@ -407,19 +521,26 @@ def main():
     ap.add_argument("--size", default="1024x1024x512")
     ap.add_argument("--zbeta", type=float, default=BETA, help="tanh clustering of the z faces (0: uniform)")
     ap.add_argument("--refine", type=int, default=1)
-    ap.add_argument("--ref-nz", type=int, default=4, help="z levels of the oracle sample per reference step")
-    ap.add_argument("--cpu-nz", type=int, default=16, help="z levels of the cpu_baseline sample")
+    ap.add_argument("--ref-nz", type=int, default=16,
+                    help="z levels of the oracle sample per reference step (rounded up to a multiple of the host's cores)")
+    ap.add_argument("--cpu-nz", type=int, default=16,
+                    help="z levels of the cpu_baseline sample (rounded up to a multiple of the host's cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunk-mb", type=int, default=0,
+                    help="split the end-to-end host copies into chunks of this many MiB (0: one copy per field)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-viscous", action="store_true", help="skip the viscous-solve measurement")
     ap.add_argument("--autotune", type=int, default=0, help="1: plan-time autotuning of the launch shapes")
     ap.add_argument("--tuning", default="", help="JSON dict of ibf_tuning fields forced for the mixed plan")
-    ap.add_argument("--batch64", action="store_true", help="time the 64-grid batched workload instead")
+    ap.add_argument("--batch64", action="store_true", help="time the 64-grid batched workload alone")
+    ap.add_argument("--no-batch64", action="store_true", help="skip the 64-grid batched measurement")
+    ap.add_argument("--no-autotune-batch", action="store_true", help="default launch shapes for the 64 grids")
     ap.add_argument("--cpu-child", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_child:
-        cpu_baseline_child(args.cpu_child)
+        cpu_baseline_child(args.cpu_child, args.cpu_reps)
         return 0
     if args.impl == "reference":
         return reference_arm(args)
@@ -511,9 +632,24 @@ def main():
     }
     if FP64 in res:
         f = res[FP64]
+        flops = fp64_flops_per_cell(nx, ny)
+        tf_peak, tf_kind, dadd_gops = fp64_peak()
+        fk = {k: {"launches": c, "ms_per_launch": t / c,
+                  "tflops_algorithmic": flops.get(k, 0.0) * cells / (t / c * 1e-3) / 1e12}
+              for k, (c, t) in f["prof"].items()}
+        fd = max(((k, v) for k, v in f["prof"].items() if flops.get(k, 0.0) > 0), key=lambda kv: kv[1][1])
+        fdn, (fdc, fdt) = fd
+        f_ach = flops[fdn] * cells / (fdt / fdc * 1e-3) / 1e12
+        f_step = sum(flops.get(k, 0.0) * c / args.steps for k, (c, _) in f["prof"].items())
         line["fp64"] = {"value": ws * cells / (f["ms"] * 1e-3), "ms_per_step": f["ms"],
-                        "kernels": {k: {"launches": c, "ms_per_launch": t / c} for k, (c, t) in f["prof"].items()},
-                        "speedup_mixed_over_fp64": f["ms"] / ms}
+                        "kernels": fk, "speedup_mixed_over_fp64": f["ms"] / ms,
+                        "roofline": {"bound": "alu", "pipe": "fp64", "kernel": fdn, "achieved": f_ach,
+                                     "peak": tf_peak, "unit": "TFLOP/s", "frac": f_ach / tf_peak,
+                                     "peak_kind": tf_kind, "flops_per_cell": flops[fdn],
+                                     "peak_nominal": FP64_NOMINAL_TFLOPS, "dadd_gops": dadd_gops},
+                        "projection_alu": {"flops_per_cell_model": f_step,
+                                           "achieved_tflops": f_step * cells / (f["ms"] * 1e-3) / 1e12,
+                                           "frac": f_step * cells / (f["ms"] * 1e-3) / 1e12 / tf_peak}}
 
     # End to end through the public API with host buffers (pinned), copies inside the timed
     # region: every step uploads its own u*, v*, w* and downloads its own u, v, w, phi.  Steps
@@ -543,7 +679,7 @@ def main():
                     if projected[b_] is not None:
                         s_up.wait_event(projected[b_])
                     for d, h in zip(d_in, h_in):
-                        d.copy_(h, non_blocking=True)
+                        chunked_copy(d, h, chunk)
                     up = torch.cuda.Event()
                     up.record(s_up)
                 s_comp.wait_event(up)
@@ -556,13 +692,14 @@ def main():
                 with torch.cuda.stream(s_down):
                     s_down.wait_event(done)
                     for h, d in zip(h_out, d_out):
-                        h.copy_(d, non_blocking=True)
+                        chunked_copy(h, d, chunk)
                     dn = torch.cuda.Event()
                     dn.record(s_down)
                     downloaded[b_] = dn
             s_comp.wait_stream(s_down)
             s_comp.wait_stream(s_up)
 
+        chunk = args.e2e_chunk_mb << 20
         run_steps(2)
         torch.cuda.synchronize()
         barrier(ws)
@@ -577,9 +714,19 @@ def main():
         ems = max_over_ranks(e0.elapsed_time(e1) / ke, ws)
         line["e2e"] = {"value": ws * cells / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ke,
-                       "pipelined": "upload of step i+1 and download of step i overlap step i's projection"}
+                       "pipelined": "upload of step i+1 and download of step i overlap step i's projection",
+                       "copy_chunk_mb": args.e2e_chunk_mb or None,
+                       "link": host_link_rates(h_in[0], h_out[0], dev_sets[1][0][0], dev_sets[1][1][0])}
+        lk = line["e2e"]["link"]
+        line["e2e"]["link_bound_ms"] = max(h2d / lk["h2d_gbs"], d2h / lk["d2h_gbs"],
+                                           (h2d + d2h) / lk["both_gbs"]) / 1e6
         line["gpu_launches"] += int(round(launches_per_step * ke))
         del dev_sets, h_in, h_out
+
+    # the batched workload (64 uneven grids, autotuned; separate object: not the headline)
+    if not args.no_batch64:
+        line["batch64"] = measure_batch64(args, ws, rank, dev, autotune=not args.no_autotune_batch)
+        line["gpu_launches"] += line["batch64"]["gpu_launches"]
 
     # the factored implicit viscous solve on the same workload and plans (separate object:
     # not part of the projection's step)
@@ -598,7 +745,7 @@ def main():
         r["plan"].close()
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        nzs = min(args.cpu_nz, nz)
+        nzs = host_sample_nz(args.cpu_nz, nz)
         cb, err = run_cpu_baseline(nx, ny, nzs)
         if cb is not None:
             line["cpu_baseline"] = {"value": cb["cells"] / cb["seconds"], "unit": "cells/s", "cores": cb["cores"],

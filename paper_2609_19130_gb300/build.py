@@ -1,4 +1,7 @@
-"""Build libibf.so (sm_103a) in-tree with nvcc: the translation units compiled in parallel."""
+"""Build libibf.so (sm_103a) in-tree with nvcc: the translation units compiled in parallel.
+
+Beside it, libibf_probe.so: the fp64-pipe throughput probe that bench.py uses as the
+denominator of the fp64 path's roofline (not part of the projection library)."""
 import os
 import subprocess
 import sys
@@ -8,6 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libibf.so")
+PROBE_LIB = os.path.join(OUT_DIR, "libibf_probe.so")
+PROBE_SOURCE = "ibf_probe.cu"
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -23,7 +28,9 @@ def _nvcc():
 
 
 def _stale():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
+        return True
+    if os.path.getmtime(PROBE_LIB) < os.path.getmtime(os.path.join(CSRC, PROBE_SOURCE)):
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "ibf.h")]
@@ -49,11 +56,12 @@ def build(force=False, verbose=False):
         subprocess.check_call(cmd)
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-    os.replace(tmp, LIB)
+    with ThreadPoolExecutor(len(SOURCES) + 1) as ex:
+        objs = list(ex.map(compile_one, SOURCES + [PROBE_SOURCE]))
+    for lib, o in ((LIB, objs[:-1]), (PROBE_LIB, objs[-1:])):
+        tmp = lib + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + o + ["-lcudart"])
+        os.replace(tmp, lib)
     return LIB
 
 
