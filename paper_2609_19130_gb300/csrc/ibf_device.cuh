@@ -85,6 +85,17 @@ __device__ __forceinline__ df sum3(float a, float b, float c) {
     return two_sum(t.hi, __fadd_rn(t.lo, s.lo));
 }
 
+// hi + lo + v for a possibly unnormalised pair (hi, lo) as a normalised pair: hi + v
+// and its error, that error plus lo and its error, all without rounding, then the
+// leading float renormalised against the collected remainder (error below 2^-47 of the
+// sum, whatever the relative sizes of lo and v)
+__device__ __forceinline__ df df_add3(float hi, float lo, float v) {
+    const df s = two_sum(hi, v);
+    const df t = two_sum(s.lo, lo);
+    const df u = two_sum(s.hi, t.hi);
+    return quick_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+
 // the same sum as an unnormalised pair: hi the rounded sum, lo its error (rounded once)
 __device__ __forceinline__ df sum3u(float a, float b, float c) {
     const df s = two_sum(a, b);

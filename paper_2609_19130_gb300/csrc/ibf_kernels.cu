@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
             float Pm = 0.f, Pc = 0.f;
             bool have = false;
             df2 acc2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of phi, per lane
+            df2 accr = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of the residual, per lane
             for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
                 float pn[kRowGroup], pkp[kRowGroup], pkm[kRowGroup], peu[kRowGroup], ped[kRowGroup];
                 float2 bdv[kRowGroup];
@@ -377,6 +378,8 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                     const float2 val = p2mul(p2add(r.hi, r.lo), make_float2(scale, scale));
                     const bool u0 = act && live[0], u1 = act && live[1];
                     acc2 = df_addf2(acc2, make_float2(u0 ? pc[0] : 0.f, u1 ? pc[1] : 0.f));
+                    accr = df_add2(accr, df2{make_float2(u0 ? r.hi.x : 0.f, u1 ? r.hi.y : 0.f),
+                                             make_float2(u0 ? r.lo.x : 0.f, u1 ? r.lo.y : 0.f)});
                     if (act) {
                         const float v0 = u0 ? val.x : 0.f, v1 = u1 ? val.y : 0.f;
                         float *slot = reinterpret_cast<float *>(buf + (jl0 >> 1) * sstride + spos);
@@ -391,6 +394,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                 }
             }
             acc_phi = df_add(acc_phi, df_add(df{acc2.hi.x, acc2.lo.x}, df{acc2.hi.y, acc2.lo.y}));
+            acc = df_add(acc, df_add(df{accr.hi.x, accr.lo.x}, df{accr.hi.y, accr.lo.y}));
         } else {
             PhiSrc<A> ph;
             if constexpr (sizeof(T) == 4) {
@@ -454,6 +458,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                             if constexpr (sizeof(T) == 4) bvv = df{bdv[q].x, bdv[q].y};
                             const V bv = A::sub(A::sub(bvv, cp), lap);
                             acc_phi = A::add(acc_phi, Pc);
+                            acc = A::add(acc, bv);
                             val = to_T<T, A>(bv) * scale;
                         }
                         Pm = Pc;
@@ -468,14 +473,16 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
         }
     }
     // plane sums of this block's rows (for the singular mode), fixed reduction order:
-    // of the right-hand side in the first pass; of phi in a refinement pass (k_00 forms
-    // the plane means of the residual from both, since x and y differences sum to zero
-    // over a plane).  With the split, a slot per half row block.
+    // of the right-hand side in the first pass; of the residual and of phi in a
+    // refinement pass.  k_00 takes the (0,0) mode of the correction from the residual's
+    // plane means (small once phi is close, so their rounding is small too) and the
+    // weighted mean of phi from phi's.  With the split, a slot per half row block.
     const int pslot = G.part_off + (k * nrb + rb) * SPLIT + half;
-    if (DIVL || MODE == XM_ADJ) {
+    if (MODE != XM_COPY) {
         V tot = Red<A>::sum(acc, red);
         if (threadIdx.x == 0) w.partial[pslot] = A::store(tot);
-    } else if (MODE != XM_COPY) {
+    }
+    if (MODE == XM_RESID || MODE == XM_RESID0) {
         V totp = Red<A>::sum(acc_phi, red);
         if (threadIdx.x == 0) w.partial_phi[pslot] = A::store(totp);
     }
@@ -658,8 +665,10 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
             } else if (!lo_valid) {
                 phl[t] = (float)val;  // phi = phi_0 + delta held as the unevaluated pair (hi, lo)
             } else {
-                const df cur = {phh[t], phl[t]};
-                const df nw = df_addf(cur, (float)val);
+                // (hi, lo) may be unnormalised (lo = the first correction, larger than an
+                // ulp of hi): hi + lo + val is formed without error in three floats and
+                // rounded once into a normalised pair, so the correction keeps its low bits
+                const df nw = df_add3(phh[t], phl[t], (float)val);
                 phh[t] = nw.hi;
                 phl[t] = nw.lo;
             }

@@ -680,8 +680,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_zsweep(Work w) {
 // ================================================================ k_00 (fp64, one CTA per grid)
 template <typename T>
 __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
-    // Shared memory: right-hand side, hz, and two copies (ping-pong) of the four PCR
-    // arrays a, b, c, d; every array has nz+1 entries.
+    // Shared memory: right-hand side, hz, the flux terms hz_k d_k, their running sums,
+    // the increments of phi, phi, and the plane means of the phi being refined; every
+    // array has nz+1 entries (the plan reserves ten).
     extern __shared__ double sh00[];
     __shared__ double red[8];
     const int g = blockIdx.x;
@@ -690,9 +691,9 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     const int L = nz + 1;
     double *rhs = sh00, *hz = sh00 + L;
     double *A0 = sh00 + 2 * L, *B0 = A0 + L, *C0 = B0 + L, *D0 = C0 + L;
-    double *A1 = D0 + L, *B1 = A1 + L, *C1 = B1 + L, *D1 = C1 + L;
+    double *A1 = D0 + L;
     const double *part = w.partial + G.part_off, *partp = w.partial_phi + G.part_off;
-    double *Pk = A1;  // plane means of the phi being refined (A1 is free until the PCR steps)
+    double *Pk = A1;  // plane means of the phi being refined
     double loc = 0.0, locp = 0.0;
     bool bad = false;
     // np slots per plane (one per row block, two with the half-block forward x-FFT CTAs),
@@ -701,7 +702,7 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         double S = 0.0;
         for (int r = 0; r < np; ++r) S += part[k * np + r];
-        const double m = S * G.inv_nxy;  // plane mean of the first right-hand side b
+        const double m = S * G.inv_nxy;  // plane mean of b (first solve) or of the residual
         if (!isfinite(m)) bad = true;
         const double h = w.z.hz[zo + k];
         rhs[k] = m;
@@ -715,20 +716,11 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     }
     if (bad) atomicOr(w.err, 1u << 6);  // IBF_ERR_NONFINITE
     __syncthreads();
-    if (!first_solve) {
-        // plane mean of the refinement residual b - <b> - L phi: the x and y differences of
-        // L phi sum to zero over a plane (periodic wrap or Neumann walls), so it is the
-        // plane mean of b, less <b>, less the z part of L applied to the plane means of phi
-        const double mb = w.mean_b[g];
-        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-            double lz = 0.0;
-            if (k + 1 < nz) lz += w.z.cz[zo + k] * (Pk[k + 1] - Pk[k]);
-            else lz -= G.ez_top * Pk[k];  // Dirichlet outlet (ez_top = 0 with a Neumann top)
-            if (k > 0) lz -= w.z.az[zo + k] * (Pk[k] - Pk[k - 1]);
-            rhs[k] = rhs[k] - mb - lz;
-        }
-        __syncthreads();
-    }
+    // In a refinement pass rhs[k] is already the plane mean of the residual
+    // b - <b> - L phi (summed from its per-cell values, which are small once phi is
+    // close): forming it instead from the plane means of b and of phi would carry the
+    // rounding of phi's plane means, amplified by the z part of L (up to 1/(hz gz) next
+    // to a stretched wall), into the correction.
     for (int k = threadIdx.x; k < nz; k += blockDim.x) loc += hz[k] * rhs[k];
     const double tot = Red<F64Arith>::sum(loc, red);
     // weighted mean of the phi being refined: the correction also removes it, so that
@@ -745,47 +737,43 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
         // compatibility defect large compared with the plane means -> warning
         if (fabs(mean) > 1e-8 * scale && fabs(mean) > 0.0) atomicOr(w.err, 1u << 7);
     }
-    // Pinned system (level 0 fixed to zero, so row 0 reads phi_0 = 0) solved by
-    // parallel cyclic reduction (Hockney 1965): each step eliminates from every row its
-    // couplings at distance st; after ceil(log2 nz) steps row k reads phi_k = d_k / b_k.
-    // Row k of L along z: a = az_k (to k-1), b = -(az_k + cz_k), c = cz_k (to k+1).
-    // With a Dirichlet outlet every row is regular (row nz-1 gains the outlet flux term).
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        if (k == 0 && !G.dir_top) { A0[k] = 0.0; B0[k] = 1.0; C0[k] = 0.0; D0[k] = 0.0; }
-        else {
-            const double a = w.z.az[zo + k], c = w.z.cz[zo + k];
-            const double ez = (k == nz - 1) ? G.ez_top : 0.0;
-            A0[k] = a; B0[k] = -(a + c) - ez; C0[k] = c; D0[k] = rhs[k] - mean;
+    // The (0,0) system in flux form.  Row k of L along z, times hz_k, is a difference of
+    // face fluxes, hz_k (L phi)_k = F_{k+1/2} - F_{k-1/2} with F_{k+1/2} =
+    // (phi_{k+1} - phi_k) / gz_{k+1} and F_{-1/2} = 0 at the bottom wall, so
+    //   F_{k+1/2} = S_k = sum_{j <= k} hz_j d_j,      d = right-hand side less its mean,
+    //   phi_k     = phi_{k+1} - gz_{k+1} S_k          (integrated down from level nz-1).
+    // Neumann top: the top flux is zero (S_{nz-1} = 0 up to rounding, since d has zero
+    // weighted mean), phi_{nz-1} is pinned to 0 and the weighted mean removed below.
+    // Dirichlet outlet: the top flux is -hz_{nz-1} ez_top phi_{nz-1} = S_{nz-1}, which
+    // fixes phi_{nz-1}.  The two running sums are the exact solve of the system; unlike
+    // an elimination on the rows a_k, -(a_k + c_k), c_k (whose reduced diagonals cancel
+    // by orders of magnitude on a stretched grid) they leave a residual at the rounding
+    // of the fluxes.  Sums in one thread, the divisions by 1/gz in parallel.
+    double *S = B0, *inc = C0;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) A0[k] = hz[k] * (rhs[k] - mean);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int k = 0; k < nz; ++k) {
+            acc += A0[k];
+            S[k] = acc;
         }
     }
     __syncthreads();
-    for (int st = 1; st < nz; st <<= 1) {
-        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-            double na = 0.0, nb = B0[k], nc = 0.0, nd = D0[k];
-            if (k - st >= 0) {
-                const double al = -A0[k] / B0[k - st];
-                na = al * A0[k - st];
-                nb += al * C0[k - st];
-                nd += al * D0[k - st];
-            }
-            if (k + st < nz) {
-                const double ga = -C0[k] / B0[k + st];
-                nc = ga * C0[k + st];
-                nb += ga * A0[k + st];
-                nd += ga * D0[k + st];
-            }
-            A1[k] = na; B1[k] = nb; C1[k] = nc; D1[k] = nd;
+    for (int k = threadIdx.x; k + 1 < nz; k += blockDim.x) inc[k] = S[k] / w.z.rgzf[zo + k + 1];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ph = G.dir_top ? -S[nz - 1] / (hz[nz - 1] * G.ez_top) : 0.0;
+        D0[nz - 1] = ph;
+        for (int k = nz - 2; k >= 0; --k) {
+            ph -= inc[k];
+            D0[k] = ph;
         }
-        __syncthreads();
-        double *t;
-        t = A0; A0 = A1; A1 = t;
-        t = B0; B0 = B1; B1 = t;
-        t = C0; C0 = C1; C1 = t;
-        t = D0; D0 = D1; D1 = t;
     }
+    __syncthreads();
     double lsv = 0.0;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        const double ph = D0[k] / B0[k];
+        const double ph = D0[k];
         rhs[k] = ph;
         lsv += hz[k] * ph;
     }
