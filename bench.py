@@ -38,10 +38,25 @@ SEED = 4
 # Algorithmic HBM bytes per cell of each kernel (fp64 user fields, fp32 spectrum of
 # ~4 B per cell, float-float right-hand side): x_forward_div reads u*, v*, w* (24) and
 # writes b (8) and the spectrum (4); a y/z pass reads and writes the spectrum and reads
-# the fp32 pivot table (4 + 4 + 2); the residual reads phi_0 and b (4 + 8) and writes the
-# spectrum; the correction reads u*, v*, w*, phi (24 + 8) and writes u, v, w, phi (24 + 8).
+# the fp32 pivot table (4 + 4 + 2); the inverse x-FFT reads the spectrum and writes phi_0
+# (4 + 4); the first sweep's residual reads phi_0 and b (4 + 8) and writes the spectrum,
+# its accumulation reads the spectrum and writes the low word of phi (4 + 4); a later
+# sweep's residual reads the float-float phi and b (8 + 8) and writes the spectrum, its
+# accumulation reads the spectrum and phi and writes phi (4 + 8 + 8); the correction reads
+# u*, v*, w*, phi (24 + 8) and writes u, v, w, phi (24 + 8).
 BYTES_MIXED = {"x_forward_div": 36.0, "yz_forward": 10.0, "yz_backward": 10.0, "x_inverse_store": 8.0,
-               "x_forward_residual": 16.0, "x_inverse_accumulate": 16.0, "correct": 64.0, "mode00": 0.0}
+               "x_forward_residual": 16.0, "x_inverse_accumulate": 8.0, "x_forward_residual2": 20.0,
+               "x_inverse_accumulate2": 20.0, "x_inverse_last": 8.0, "correct": 64.0, "mode00": 0.0}
+# with two or more sweeps the last correction is kept apart (phi = hi + lo + lo2): the last
+# sweep's inverse x-FFT writes lo2 (4 + 4) and the correction also reads it (64 + 4)
+BYTES_CORRECT_LO2 = 68.0
+
+
+def bytes_mixed(refine):
+    b = dict(BYTES_MIXED)
+    if refine >= 2:
+        b["correct"] = BYTES_CORRECT_LO2
+    return b
 BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x_inverse_store": 16.0,
               "correct": 56.0, "mode00": 0.0}
 # fp64 path: its transforms and sweeps keep the fp64 pipe busy, so its roofline is that
@@ -520,7 +535,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", default="1024x1024x512")
     ap.add_argument("--zbeta", type=float, default=BETA, help="tanh clustering of the z faces (0: uniform)")
-    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--refine", type=int, default=2,
+                    help="refinement sweeps of the headline mixed run (two reach the fp64 round-off floor of the "
+                         "divergence on the benchmark's stretched grid; one meets the bound on phi only)")
+    ap.add_argument("--no-one-sweep", action="store_true", help="skip the one-sweep comparison run")
     ap.add_argument("--ref-nz", type=int, default=16,
                     help="z levels of the oracle sample per reference step (rounded up to a multiple of the host's cores)")
     ap.add_argument("--cpu-nz", type=int, default=16,
@@ -573,23 +591,39 @@ def main():
                  else "L2 flushed (256 MB written) before every timed step, outside its events")
     res = {}
     clocks = None
-    for prec in ([MIXED] + ([] if args.no_fp64 else [FP64])):
+    # the headline (mixed, --refine sweeps), the fp64 path, and one sweep for comparison;
+    # outside the timed regions each run's phi and max|D u| are kept for the accuracy notes
+    runs = [("mixed", MIXED, args.refine)] + ([] if args.no_fp64 else [("fp64", FP64, 0)])
+    if args.refine != 1 and not args.no_one_sweep:
+        runs.append(("mixed_1sweep", MIXED, 1))
+    phis = {}
+    for key, prec, R in runs:
         tun = [json.loads(args.tuning)] if (args.tuning and prec == MIXED) else None
-        plan = Plan([g], precision=prec, refine_steps=args.refine if prec == MIXED else 0, device=dev.index,
+        plan = Plan([g], precision=prec, refine_steps=R, device=dev.index,
                     autotune=bool(args.autotune), tuning=tun)
-        if prec == MIXED:
+        if key == "mixed":
             with Clocks(dev.index) as ck:
                 ms, prof = time_steps(plan, ins, outs, args.steps, args.warmup, ws, flush)
             clocks = ck.summary()
-            # diagnostics outside the timed region: divergence of the output
-            (_, st) = plan.project_batch([ins], DT, out=[outs], stats=True)
-            torch.cuda.synchronize()
-            diag = {"max_div_out": float(st["max_div"][0]), "max_div_in": float(st["max_div_in"][0]),
-                    "status": plan.sync_status()}
         else:
             ms, prof = time_steps(plan, ins, outs, args.steps, args.warmup, ws, flush)
-            diag = None
-        res[prec] = {"ms": ms, "prof": prof, "diag": diag, "plan": plan, "tuning": plan.tuning(0)}
+        # diagnostics outside the timed region: divergence of the output, phi kept
+        (_, st) = plan.project_batch([ins], DT, out=[outs], stats=True)
+        torch.cuda.synchronize()
+        diag = {"max_div_out": float(st["max_div"][0]), "max_div_in": float(st["max_div_in"][0]),
+                "div_rel": float(st["max_div"][0]) / max(float(st["max_div_in"][0]), 1e-300),
+                "status": plan.sync_status()}
+        phis[key] = outs[3].clone()
+        res[key] = {"ms": ms, "prof": prof, "diag": diag, "plan": plan, "tuning": plan.tuning(0), "refine": R}
+    if "fp64" in phis:
+        ref = phis["fp64"]
+        for key in res:
+            if key != "fp64":
+                res[key]["diag"]["phi_rel_l2_vs_fp64"] = float(torch.linalg.norm(phis[key] - ref) / torch.linalg.norm(ref))
+    del phis
+    res[MIXED] = res.pop("mixed")
+    if "fp64" in res:
+        res[FP64] = res.pop("fp64")
 
     mixed = res[MIXED]
     ms = mixed["ms"]
@@ -600,14 +634,15 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dname, (dcount, dms) = dom
     per_launch_ms = dms / dcount
-    per_launch_bytes = BYTES_MIXED.get(dname, 0.0) * cells
+    BM = bytes_mixed(args.refine)
+    per_launch_bytes = BM.get(dname, 0.0) * cells
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
     traffic = None
     if dname in NCU_TRAFFIC_B_PER_CELL and NCU_SOURCES_SHA256 == kernel_sources_sha256():
         traffic = NCU_TRAFFIC_B_PER_CELL[dname] * cells
-    bytes_model = sum(BYTES_MIXED[k] * c / args.steps for k, (c, _) in prof.items() if k in BYTES_MIXED)
+    bytes_model = sum(BM[k] * c / args.steps for k, (c, _) in prof.items() if k in BM)
     kernels = {k: {"launches": c, "ms_per_launch": t / c, "share": t / sum(x[1] for x in prof.values()),
-                   "gbs_algorithmic": (BYTES_MIXED.get(k, 0.0) * cells / (t / c * 1e-3) / 1e9)}
+                   "gbs_algorithmic": (BM.get(k, 0.0) * cells / (t / c * 1e-3) / 1e9)}
                for k, (c, t) in prof.items()}
 
     line = {
@@ -620,7 +655,7 @@ def main():
                    "l2_policy": l2_policy}),
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "bytes_per_cell": BYTES_MIXED.get(dname, 0.0)},
+                     "bytes_per_cell": BM.get(dname, 0.0)},
         "projection_hbm": {"bytes_per_cell_model": bytes_model,
                            "achieved_gbs": bytes_model * cells / (ms * 1e-3) / 1e9,
                            "frac": bytes_model * cells / (ms * 1e-3) / 1e9 / hbm_peak,
@@ -647,9 +682,17 @@ def main():
                                      "peak": tf_peak, "unit": "TFLOP/s", "frac": f_ach / tf_peak,
                                      "peak_kind": tf_kind, "flops_per_cell": flops[fdn],
                                      "peak_nominal": FP64_NOMINAL_TFLOPS, "dadd_gops": dadd_gops},
+                        "diagnostics": f["diag"],
                         "projection_alu": {"flops_per_cell_model": f_step,
                                            "achieved_tflops": f_step * cells / (f["ms"] * 1e-3) / 1e12,
                                            "frac": f_step * cells / (f["ms"] * 1e-3) / 1e12 / tf_peak}}
+
+    if "mixed_1sweep" in res:
+        r1 = res["mixed_1sweep"]
+        line["mixed_1sweep"] = {
+            "value": ws * cells / (r1["ms"] * 1e-3), "ms_per_step": r1["ms"], "refine_steps": 1,
+            "diagnostics": r1["diag"],
+            "kernels": {k: {"launches": c, "ms_per_launch": t / c} for k, (c, t) in r1["prof"].items()}}
 
     # End to end through the public API with host buffers (pinned), copies inside the timed
     # region: every step uploads its own u*, v*, w* and downloads its own u, v, w, phi.  Steps
@@ -735,6 +778,8 @@ def main():
                 "workload": f"{nx}x{ny}x{nz}: (I - beta Lz)^-1 (I - beta Ly)^-1 (I - beta Lx)^-1 of u, v, w "
                             f"(the same fields as right-hand sides)"}
         for prec, r in res.items():
+            if prec not in (MIXED, FP64):
+                continue
             visc["mixed" if prec == MIXED else "fp64"] = measure_viscous(
                 r["plan"], ins, outs, args.steps, args.warmup, ws, prec == MIXED, cells, hbm_peak)
         if rank == 0 and ws == 1 and not args.no_cpu_baseline:

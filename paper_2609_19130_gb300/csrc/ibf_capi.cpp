@@ -581,6 +581,7 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         IBF_TRY(dalloc(pl, &w.bdf, sizeof(float2) * (size_t)cells));
         IBF_TRY(dalloc(pl, &w.phi_hi, sizeof(float) * (size_t)cells));
         IBF_TRY(dalloc(pl, &w.phi_lo, sizeof(float) * (size_t)cells));
+        if (pl->opts.refine_steps >= 2) IBF_TRY(dalloc(pl, &w.phi_lo2, sizeof(float) * (size_t)cells));
     } else {
         IBF_TRY(dalloc(pl, &w.phi_ws, sizeof(double) * (size_t)cells));
     }
@@ -763,18 +764,27 @@ ibf_status run(ibf_plan *pl, const ibf_fields *in, const ibf_fields *out, double
     IBF_TRY(for_chunks(c, "x_inverse_store", in, out, [&](const UserPtrs &p, int nb) {
         return launch_xinv(mixed, IM_STORE, w, p, use_ws, 0, nb, pl->xsmem, st);
     }));
+    // Sweep r adds its correction delta to phi: the first into the low word of the pair
+    // (phi_0, delta), the middle ones by an exact renormalising sum, the last one (two or
+    // more sweeps) into phi_lo2, which the correction kernel adds to the pair.
+    const int lo2 = R >= 2;
     for (int r = 0; r < R; ++r) {
         const int lo_valid = r > 0;
-        IBF_TRY(for_chunks(c, "x_forward_residual", in, out, [&](const UserPtrs &p, int nb) {
+        const bool last = lo2 && r == R - 1;
+        // the first sweep's kernels (phi_0 plain fp32) and the later ones' (float-float
+        // phi) are profiled under their own names
+        IBF_TRY(for_chunks(c, lo_valid ? "x_forward_residual2" : "x_forward_residual", in, out,
+                           [&](const UserPtrs &p, int nb) {
             return launch_xfwd(mixed, XM_RESID, w, p, use_ws, lo_valid, nb, s, rs, pl->xsmem, st);
         }));
         IBF_TRY(solve_core(c, 0));
-        IBF_TRY(for_chunks(c, "x_inverse_accumulate", in, out, [&](const UserPtrs &p, int nb) {
-            return launch_xinv(mixed, IM_ACCUM, w, p, use_ws, lo_valid, nb, pl->xsmem, st);
+        IBF_TRY(for_chunks(c, last ? "x_inverse_last" : (lo_valid ? "x_inverse_accumulate2" : "x_inverse_accumulate"),
+                           in, out, [&](const UserPtrs &p, int nb) {
+            return launch_xinv(mixed, last ? IM_LAST : IM_ACCUM, w, p, use_ws, lo_valid, nb, pl->xsmem, st);
         }));
     }
     IBF_TRY(for_chunks(c, adjoint ? "correct_adjoint" : "correct", in, out, [&](const UserPtrs &p, int nb) {
-        return launch_correct(mixed, adjoint, w, p, use_ws, R > 0, nb, s, pmode, cimp, st);
+        return launch_correct(mixed, adjoint, w, p, use_ws, R > 0, lo2, nb, s, pmode, cimp, st);
     }));
     if (!adjoint && stats && (stats->max_div || stats->max_div_in || stats->compat)) {
         if (stats->max_div) {

@@ -107,6 +107,9 @@ struct Work {
     double *phi_ws;            // per-cell fp64 phi of the adjoint solve / of a pressure update (fp64 path)
     double *bws;               // per-cell fp64 right-hand side (fp64 path with the implicit pressure update)
     float *phi_hi, *phi_lo;    // per-cell float-float phi being refined (mixed path)
+    float *phi_lo2;            // per-cell correction of the last refinement sweep, kept apart so that
+                               // phi = hi + lo + lo2 carries more bits than a float-float pair
+                               // (mixed path with two or more sweeps; else null)
     double *partial;           // per (grid, k, row block, half with xfwd_split) plane sums of the right-hand side
     double *partial_phi;       // the same of the current phi (refinement)
     double *mean_b;            // [ngrids] removed weighted mean of the first right-hand side
@@ -130,7 +133,7 @@ struct UserPtrs {
 // float-float pair), adjoint source, refinement residual of the first sweep (phi plain fp32)
 enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2, XM_RESID0 = 3, XM_DIVQ = 4 /* XM_DIV with a mass source q */,
              XM_COPY = 5 /* the field in_u itself (viscous solve): no stencil, no plane sums */ };
-enum InvMode { IM_STORE = 0, IM_ACCUM = 1 };
+enum InvMode { IM_STORE = 0, IM_ACCUM = 1, IM_LAST = 2 /* the last sweep's correction into phi_lo2 */ };
 
 // Launchers (ibf_kernels.cu).  T = 0: fp64 path, 1: mixed path.
 cudaError_t launch_xfwd(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
@@ -144,8 +147,9 @@ cudaError_t launch_zsweep(int mixed, int backward, const Work &w, int nblk, cuda
 cudaError_t launch_zdct(int mixed, const Work &w, int nblk, size_t smem, cudaStream_t st);
 cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, int use_ws, int lo_valid, int nblk,
                         size_t smem, cudaStream_t st);
+// lo2: phi is hi + lo + lo2 (the last sweep's correction in phi_lo2; mixed path, two or more sweeps)
 cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
-                           int nblk, double s, int pmode, double cimp, cudaStream_t st);
+                           int lo2, int nblk, double s, int pmode, double cimp, cudaStream_t st);
 cudaError_t launch_divstat(int mixed, const Work &w, const UserPtrs &p, int nblk, cudaStream_t st);
 cudaError_t launch_finalize(const Work &w, double *max_div, double *max_div_in, double *compat, double s,
                             cudaStream_t st);

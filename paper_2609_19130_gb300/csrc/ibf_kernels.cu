@@ -650,11 +650,12 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
     const ptrdiff_t base = (ptrdiff_t)k * plane + (ptrdiff_t)j0 * nx;
     const int ncell = max(0, min(rows, ny - j0)) * nx;
     double *phi64 = nullptr;
-    float *phh = nullptr, *phl = nullptr;
+    float *phh = nullptr, *phl = nullptr, *pl2 = nullptr;
     if (sizeof(T) == 8) phi64 = (use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi]) + base;
     else {
         phh = w.phi_hi + G.cell_off + base;
         phl = w.phi_lo + G.cell_off + base;
+        if (IMODE == IM_LAST) pl2 = w.phi_lo2 + G.cell_off + base;
     }
     auto put = [&](int t, T val) {
         if constexpr (sizeof(T) == 8) {
@@ -662,6 +663,8 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
         } else {
             if (IMODE == IM_STORE) {
                 phh[t] = (float)val;
+            } else if (IMODE == IM_LAST) {
+                pl2[t] = (float)val;  // phi = hi + lo + lo2, read so by the correction
             } else if (!lo_valid) {
                 phl[t] = (float)val;  // phi = phi_0 + delta held as the unevaluated pair (hi, lo)
             } else {
@@ -706,10 +709,13 @@ constexpr int kRowGroupC = 2;
 // adjoint (ADJ = 1): g* = g_u + hz_k rdx (psi_{i-1} - psi_i), ...,
 //                    w_k = g_w,k + psi_{k-1} [k>=1] - psi_k [k<=nz-1].
 // PU: forward with a pressure update (pmode 1: p_n + phi, 2: minus cimp (b - <b>)).
-template <class A, int ADJ, bool W, bool PU>
+// L2 (mixed path, two or more sweeps): phi is hi + lo + lo2, with lo2 the last sweep's
+// correction in phi_lo2; its differences are formed in fp32 beside those of the pair (lo2
+// is a few 1e-10 of phi, so they round far below the pair's last bit) and added to them.
+template <class A, int ADJ, bool W, bool PU, bool L2 = false>
 // mixed: five CTAs per SM (48 registers; a few spilled bytes cost less than the fifth
-// CTA's latency hiding gains on the loads); fp64: room for the pressure terms
-__global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 5 : 3)
+// CTA's latency hiding gains on the loads), four with lo2; fp64: room for the pressure terms
+__global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? (L2 ? 4 : 5) : 3)
     k_correct(Work w, UserPtrs p, int use_ws, int lo_valid, double s, int pmode, double cimp) {
     typedef typename A::V V;
     const int b = blockIdx.x + p.blk0;
@@ -726,9 +732,11 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 5 : 3)
     const ptrdiff_t pbase = (ptrdiff_t)k * plane;
     PhiSrc<A> ph;
     constexpr bool MIX = IsDF<A>::value;
+    const float *l2p = nullptr;  // lo2 of the plane (L2)
     if constexpr (MIX) {
         ph.hi = w.phi_hi + G.cell_off + pbase;
         ph.lo = lo_valid ? w.phi_lo + G.cell_off + pbase : nullptr;
+        if (L2) l2p = w.phi_lo2 + G.cell_off + pbase;
     } else {
         ph.p = (use_ws ? (w.phi_ws + G.cell_off) : p.out_p[gi]) + pbase;
     }
@@ -765,16 +773,20 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 5 : 3)
         const bool own_dn = (lane == 0) || (ii == 0);
         const bool wall_lo = wall_x && ii == 0;  // face 0 of a wall-bounded row
         V Pjm = A::zero();
+        float L2jm = 0.f;
         bool have = false;
         for (int jg = sm.r0; jg < sm.r1; jg += kRowGroupC) {
             V pc[kRowGroupC], pkm[kRowGroupC], ped[kRowGroupC];
+            float lc[kRowGroupC], lkm[kRowGroupC], led[kRowGroupC];  // lo2 (L2)
             double ru[kRowGroupC], rv[kRowGroupC], rw[kRowGroupC], rwt[kRowGroupC];
             V pjm0 = A::zero();
+            float ljm0 = 0.f;
             const bool need0 = !have;
 #pragma unroll
             for (int q = 0; q < kRowGroupC; ++q) {
                 const int jl = jg + q, j = j0 + jl;
                 pc[q] = pkm[q] = ped[q] = A::zero();
+                lc[q] = lkm[q] = led[q] = 0.f;
                 ru[q] = rv[q] = rw[q] = rwt[q] = 0.0;
                 if (jl < sm.r1 && j < ny) {
                     const int jm = (j == 0) ? ny - 1 : j - 1;
@@ -783,6 +795,12 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 5 : 3)
                     pc[q] = ph.get(row + ii);
                     if (k > 0) pkm[q] = ph.get(row + ii - plane);
                     if (own_dn) ped[q] = ph.get(row + im);
+                    if constexpr (L2) {
+                        if (q == 0 && need0) ljm0 = __ldg(l2p + jm * nx + ii);
+                        lc[q] = __ldg(l2p + row + ii);
+                        if (k > 0) lkm[q] = __ldg(l2p + row + ii - plane);
+                        if (own_dn) led[q] = __ldg(l2p + row + im);
+                    }
                     if (act) {
                         ru[q] = ui[j * nxu + i];
                         rv[q] = vi[row + i];
@@ -791,7 +809,10 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 5 : 3)
                     }
                 }
             }
-            if (need0) Pjm = pjm0;
+            if (need0) {
+                Pjm = pjm0;
+                L2jm = ljm0;
+            }
 #pragma unroll
             for (int q = 0; q < kRowGroupC; ++q) {
                 const int jl = jg + q, j = j0 + jl;
@@ -804,25 +825,40 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 5 : 3)
                 // there sees only the one interior cell
                 if (wall_lo) Pim = ADJ ? A::zero() : Pc;
                 const V Pjw = (wall_y && j == 0) ? (ADJ ? A::zero() : Pc) : Pjm;
+                // the differences of phi (L2: of hi + lo, then those of lo2 added)
+                V dxm = A::sub(Pim, Pc), dym = A::sub(Pjw, Pc), dzm = A::sub(pkm[q], Pc);
+                V Pcn = Pc;
+                if constexpr (L2) {
+                    const float Lc = lc[q];
+                    float Lim = __shfl_up_sync(0xffffffffu, Lc, 1);
+                    if (own_dn) Lim = led[q];
+                    if (wall_lo) Lim = ADJ ? 0.f : Lc;
+                    const float Ljw = (wall_y && j == 0) ? (ADJ ? 0.f : Lc) : L2jm;
+                    dxm = df_addf(dxm, __fsub_rn(Lim, Lc));
+                    dym = df_addf(dym, __fsub_rn(Ljw, Lc));
+                    dzm = df_addf(dzm, __fsub_rn(lkm[q], Lc));
+                    Pcn = df_add3(Pc.hi, Pc.lo, Lc);
+                    L2jm = Lc;
+                }
                 if (act) {
                     // the correction t is formed in the solve's high precision; the face
                     // value u* + t is one fp64 add (the fp64 pipe is otherwise idle here)
                     const int c = row + i;
-                    uo[j * nxu + i] = ru[q] + A::store(A::mul(cu, A::sub(Pim, Pc)));
-                    vo[c] = rv[q] + A::store(A::mul(cv, A::sub(Pjw, Pc)));
+                    uo[j * nxu + i] = ru[q] + A::store(A::mul(cu, dxm));
+                    vo[c] = rv[q] + A::store(A::mul(cv, dym));
                     if (ADJ) {
-                        wo[c] = rw[q] + A::store(A::sub(pkm[q], Pc));
-                        if (k == nz - 1) wo[c + plane] = rwt[q] + A::store(A::norm(Pc));
+                        wo[c] = rw[q] + A::store(dzm);
+                        if (k == nz - 1) wo[c + plane] = rwt[q] + A::store(A::norm(Pcn));
                     } else {
                         if (k == 0) wo[c] = rw[q];
-                        else wo[c] = rw[q] + A::store(A::mul(cw, A::sub(pkm[q], Pc)));
+                        else wo[c] = rw[q] + A::store(A::mul(cw, dzm));
                         if (k == nz - 1)  // outlet face: corrected with a Dirichlet outlet, else a wall
-                            wo[c + plane] = G.dir_top ? rwt[q] + A::store(A::mul(cwt, Pc)) : rwt[q];
+                            wo[c + plane] = G.dir_top ? rwt[q] + A::store(A::mul(cwt, Pcn)) : rwt[q];
                         if (po) {
                             if constexpr (!PU) {
-                                po[c] = A::store(A::norm(Pc));
+                                po[c] = A::store(A::norm(Pcn));
                             } else {
-                                double pv = pn[c] + A::store(A::norm(Pc));
+                                double pv = pn[c] + A::store(A::norm(Pcn));
                                 if (pmode == 2) {
                                     double bb;
                                     if constexpr (MIX) {
@@ -848,13 +884,17 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? 5 : 3)
         const int nr = min(rows, ny - j0);
         for (int t = threadIdx.x; t < nr; t += blockDim.x) {
             const int j = j0 + t, f = j * nxu + nx;
-            uo[f] = ADJ ? ui[f] + A::store(A::mul(cu, ph.get(j * nx + nx - 1))) : ui[f];
+            V pf = ph.get(j * nx + nx - 1);
+            if constexpr (L2) pf = df_addf(pf, __ldg(l2p + j * nx + nx - 1));
+            uo[f] = ADJ ? ui[f] + A::store(A::mul(cu, pf)) : ui[f];
         }
     }
     if (wall_y && j0 + rows >= ny) {
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const int f = ny * nx + i;
-            vo[f] = ADJ ? vi[f] + A::store(A::mul(cv, ph.get((ny - 1) * nx + i))) : vi[f];
+            V pf = ph.get((ny - 1) * nx + i);
+            if constexpr (L2) pf = df_addf(pf, __ldg(l2p + (ny - 1) * nx + i));
+            vo[f] = ADJ ? vi[f] + A::store(A::mul(cv, pf)) : vi[f];
         }
     }
 }
@@ -967,11 +1007,15 @@ cudaError_t launch_xinv_w(int mixed, int mode, const Work &w, const UserPtrs &p,
         const dim3 gr = grid1(2 * nblk);
         if (mode == IM_STORE)
             k_xinv<float, DFArith, IM_STORE, W, 2><<<gr, kXThreads / 2, smem / 2, st>>>(w, p, use_ws, lo_valid);
+        else if (mode == IM_LAST)
+            k_xinv<float, DFArith, IM_LAST, W, 2><<<gr, kXThreads / 2, smem / 2, st>>>(w, p, use_ws, lo_valid);
         else
             k_xinv<float, DFArith, IM_ACCUM, W, 2><<<gr, kXThreads / 2, smem / 2, st>>>(w, p, use_ws, lo_valid);
     } else if (mixed) {
         if (mode == IM_STORE)
             k_xinv<float, DFArith, IM_STORE, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
+        else if (mode == IM_LAST)
+            k_xinv<float, DFArith, IM_LAST, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
         else
             k_xinv<float, DFArith, IM_ACCUM, W, 1><<<grid1(nblk), kXThreads, smem, st>>>(w, p, use_ws, lo_valid);
     } else {
@@ -989,9 +1033,13 @@ cudaError_t launch_xinv(int mixed, int mode, const Work &w, const UserPtrs &p, i
 
 template <bool W>
 cudaError_t launch_correct_w(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
-                             int nblk, double s, int pm, double ci, cudaStream_t st) {
+                             int lo2, int nblk, double s, int pm, double ci, cudaStream_t st) {
     const dim3 gr = grid1(nblk);
-    if (mixed) {
+    if (mixed && lo2) {
+        if (adjoint) k_correct<DFArith, 1, W, false, true><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, 0, 0.0);
+        else if (pm) k_correct<DFArith, 0, W, true, true><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, pm, ci);
+        else k_correct<DFArith, 0, W, false, true><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, 0, 0.0);
+    } else if (mixed) {
         if (adjoint) k_correct<DFArith, 1, W, false><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, 0, 0.0);
         else if (pm) k_correct<DFArith, 0, W, true><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, pm, ci);
         else k_correct<DFArith, 0, W, false><<<gr, kXThreads, 0, st>>>(w, p, use_ws, lo_valid, s, 0, 0.0);
@@ -1004,10 +1052,10 @@ cudaError_t launch_correct_w(int mixed, int adjoint, const Work &w, const UserPt
 }
 
 cudaError_t launch_correct(int mixed, int adjoint, const Work &w, const UserPtrs &p, int use_ws, int lo_valid,
-                           int nblk, double s, int pmode, double cimp, cudaStream_t st) {
+                           int lo2, int nblk, double s, int pmode, double cimp, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
-    return w.walls ? launch_correct_w<true>(mixed, adjoint, w, p, use_ws, lo_valid, nblk, s, pmode, cimp, st)
-                   : launch_correct_w<false>(mixed, adjoint, w, p, use_ws, lo_valid, nblk, s, pmode, cimp, st);
+    return w.walls ? launch_correct_w<true>(mixed, adjoint, w, p, use_ws, lo_valid, lo2, nblk, s, pmode, cimp, st)
+                   : launch_correct_w<false>(mixed, adjoint, w, p, use_ws, lo_valid, lo2, nblk, s, pmode, cimp, st);
 }
 
 cudaError_t launch_divstat(int mixed, const Work &w, const UserPtrs &p, int nblk, cudaStream_t st) {
@@ -1062,8 +1110,10 @@ cudaError_t set_smem_limits(int mixed) {
             set((const void *)k_xfwd<float, DFArith, XM_ADJ, W, 2>);
             set((const void *)k_xinv<float, DFArith, IM_STORE, W, 1>);
             set((const void *)k_xinv<float, DFArith, IM_ACCUM, W, 1>);
+            set((const void *)k_xinv<float, DFArith, IM_LAST, W, 1>);
             set((const void *)k_xinv<float, DFArith, IM_STORE, W, 2>);
             set((const void *)k_xinv<float, DFArith, IM_ACCUM, W, 2>);
+            set((const void *)k_xinv<float, DFArith, IM_LAST, W, 2>);
         } else {
             set((const void *)k_xfwd<double, F64Arith, XM_DIV, W, 1>);
             set((const void *)k_xfwd<double, F64Arith, XM_DIVQ, W, 1>);

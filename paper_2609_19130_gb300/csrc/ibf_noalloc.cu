@@ -198,6 +198,8 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     const size_t o_spec = cv.take(csz * nspec), o_tab = cv.take(rsz * nspec);
     const size_t o_bdf = mixed ? cv.take(8 * cells) : 0;
     const size_t o_phh = mixed ? cv.take(4 * cells) : 0, o_phl = mixed ? cv.take(4 * cells) : 0;
+    const int R = mixed ? opts->refine_steps : 0;
+    const size_t o_phl2 = (mixed && R >= 2) ? cv.take(4 * cells) : 0;
     const size_t npart = (size_t)nz * d.nrb;  // no half-block forward x-FFT CTAs here
     const size_t o_part = cv.take(8 * npart), o_partp = cv.take(8 * npart);
     const size_t o_mean = cv.take(8), o_maxb = cv.take(8), o_maxd = cv.take(8), o_err = cv.take(4);
@@ -298,6 +300,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
         w.bdf = reinterpret_cast<float2 *>(base + o_bdf);
         w.phi_hi = reinterpret_cast<float *>(base + o_phh);
         w.phi_lo = reinterpret_cast<float *>(base + o_phl);
+        if (R >= 2) w.phi_lo2 = reinterpret_cast<float *>(base + o_phl2);
     }
     w.partial = reinterpret_cast<double *>(base + o_part);
     w.partial_phi = reinterpret_cast<double *>(base + o_partp);
@@ -312,7 +315,7 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     p.out_u[0] = out->u; p.out_v[0] = out->v; p.out_w[0] = out->w; p.out_p[0] = out->p;
     p.g0 = 0; p.g1 = 1; p.blk0 = 0;
 
-    const int nxblk = nz * d.nrb, nyz = d.ncb, R = mixed ? opts->refine_steps : 0;
+    const int nxblk = nz * d.nrb, nyz = d.ncb;
     const double sc = alpha * dt, rs = 1.0 / sc;
     cudaError_t e = set_smem_limits(mixed);
     if (e == cudaSuccess) e = launch_build_table(mixed, w, nyz, st);
@@ -326,12 +329,15 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
     };
     if (e == cudaSuccess) e = solve(1);
     if (e == cudaSuccess) e = launch_xinv(mixed, IM_STORE, w, p, 0, 0, nxblk, xsmem, st);
+    // the refinement sweeps as in ibf_project: the last of two or more keeps its
+    // correction apart in phi_lo2
     for (int r = 0; r < R && e == cudaSuccess; ++r) {
         e = launch_xfwd(mixed, XM_RESID, w, p, 0, r > 0, nxblk, sc, rs, xsmem, st);
         if (e == cudaSuccess) e = solve(0);
-        if (e == cudaSuccess) e = launch_xinv(mixed, IM_ACCUM, w, p, 0, r > 0, nxblk, xsmem, st);
+        const int im = (R >= 2 && r == R - 1) ? IM_LAST : IM_ACCUM;
+        if (e == cudaSuccess) e = launch_xinv(mixed, im, w, p, 0, r > 0, nxblk, xsmem, st);
     }
-    if (e == cudaSuccess) e = launch_correct(mixed, 0, w, p, 0, R > 0, nxblk, sc, IBF_P_PHI, 0.0, st);
+    if (e == cudaSuccess) e = launch_correct(mixed, 0, w, p, 0, R > 0, R >= 2, nxblk, sc, IBF_P_PHI, 0.0, st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return IBF_ERR_CUDA;
