@@ -257,7 +257,8 @@ SmemNeed smem_need(const ibf_grid &g, int mixed, const ibf_tuning &t) {
         const size_t fwd = kYZStages * ((t.mb * sstr * csz + nslot * rsz + 15) & ~(size_t)15) + nslot * csz;
         const size_t bwd = kYZStages * ((nslot * (csz + rsz) + 15) & ~(size_t)15) + (t.mb * sstr + nslot) * csz;
         n.yz = std::max(fwd, bwd);
-        if (mixed && t.mb == 1 && g.bc_y != IBF_BC_NEUMANN) n.yz = std::max(n.yz, yz_pipe_smem(g.ny, (int)sstr));
+        if (mixed && t.mb == 1 && g.bc_y != IBF_BC_NEUMANN)
+            n.yz = std::max(n.yz, std::max(yz_pipe_smem(g.ny, (int)sstr), yz_bulk_smem(g.ny, (int)sstr)));
     } else if (t.yz_kernel == 2) {
         n.slab = (((size_t)g.nz * t.mb * sstr * csz) + 15) & ~(size_t)15;
         if (t.tri > 1) n.slab += 3 * (size_t)g.nz * nslot * rsz;
@@ -582,6 +583,10 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         IBF_TRY(dalloc(pl, &w.phi_hi, sizeof(float) * (size_t)cells));
         IBF_TRY(dalloc(pl, &w.phi_lo, sizeof(float) * (size_t)cells));
         if (pl->opts.refine_steps >= 2) IBF_TRY(dalloc(pl, &w.phi_lo2, sizeof(float) * (size_t)cells));
+        // test hook: IBF_FAULT_LOSE_COPY makes the round-based forward y/z kernel drop one
+        // plane copy, so that its bounded wait runs out and IBF_ERR_TIMEOUT is reported
+        const char *lose = getenv("IBF_FAULT_LOSE_COPY");
+        w.fault_lose_copy = (lose && atoi(lose) > 0) ? 1 : 0;
     } else {
         IBF_TRY(dalloc(pl, &w.phi_ws, sizeof(double) * (size_t)cells));
     }

@@ -66,6 +66,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 }
 // order this thread's earlier shared-memory accesses before later async-proxy writes
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 template <class A> struct IsDF { static constexpr bool value = false; };
 template <> struct IsDF<DFArith> { static constexpr bool value = true; };

@@ -30,6 +30,15 @@ inline size_t yz_pipe_smem(int ny, int sstr) {
     const size_t bwd = kPipeB * pipe_align16((size_t)sstr * 8) + 2 * pipe_align16((size_t)ny * 4) + (size_t)ny * 8;
     return fwd > bwd ? fwd : bwd;
 }
+// Round-based pipelined y/z kernels (same launch; even ny): kBulkPlanes planes per round,
+// one FFT warp each, copied as whole planes with bulk asynchronous copies into two sets
+// of buffers (the next round's planes arrive while this round is computed)
+constexpr int kBulkPlanes = 3;
+constexpr unsigned kBulkWaitLimit = 1u << 20;  // polls of an mbarrier before a copy counts as lost
+inline size_t yz_bulk_smem(int ny, int sstr) {
+    const size_t sb = pipe_align16((size_t)sstr * 8 > (size_t)ny * 8 ? (size_t)sstr * 8 : (size_t)ny * 8);
+    return 2 * kBulkPlanes * sb + 2 * kBulkPlanes * 8;
+}
 constexpr int kSlabThreads = 256;  // resident-slab y/z kernel
 constexpr int kSweepThreads = 256; // split y/z path: Thomas sweeps, one thread per mode
 // spectral z: z lines (slots of a plane) per k_zdct CTA, mixed / fp64
@@ -116,6 +125,8 @@ struct Work {
     unsigned long long *maxb;  // [ngrids] max |rhs| (double bits), for max|D u*|
     unsigned long long *maxdiv;// [ngrids] max |D u| of the output (double bits)
     unsigned *err;             // device error word (bit i: ibf_status i)
+    int fault_lose_copy;       // test hook (IBF_FAULT_LOSE_COPY): the round-based forward y/z kernel
+                               // skips one plane copy, so that its bounded wait runs out
 };
 
 // Per-launch user pointers for up to kGridsPerLaunch grids.

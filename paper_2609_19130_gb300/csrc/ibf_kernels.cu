@@ -295,89 +295,125 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
             // first refinement sweep: phi_0 is plain fp32, so the second differences are
             // exact float sums (a missing wall neighbour is replaced by the cell itself,
             // which zeroes its difference) and only the coefficient products and the
-            // final sums round, at float-float precision
-            const float *ph = w.phi_hi + G.cell_off + pbase;
+            // final sums round, at float-float precision.  (Later sweeps, whose phi is
+            // hi + lo, use the general float-float stencil below on purpose: it forms the
+            // second differences from the same float-float first differences as the
+            // velocity correction, so the rounding of those differences is in the residual
+            // the last sweep corrects and cancels in D u.  Exact second differences of each
+            // word, inconsistent with the correction, left max|D u| / max|D u*| at 1.8e-9
+            // at the bench size instead of 7e-12.)
+            constexpr int NF = 1;
+            constexpr int RG = NF == 2 ? 2 : kRowGroup;  // rows whose loads go together
+            const float *phw[2] = {w.phi_hi + G.cell_off + pbase, w.phi_lo + G.cell_off + pbase};
             const float2 *bd = w.bdf + G.cell_off + pbase;
-            float Pm = 0.f, Pc = 0.f;
+            float Pm[NF], Pc[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) Pm[f] = Pc[f] = 0.f;
             bool have = false;
             df2 acc2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of phi, per lane
             df2 accr = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of the residual, per lane
-            for (int jg = sm.r0; jg < sm.r1; jg += kRowGroup) {
-                float pn[kRowGroup], pkp[kRowGroup], pkm[kRowGroup], peu[kRowGroup], ped[kRowGroup];
-                float2 bdv[kRowGroup];
-                float pm0 = 0.f, pc0 = 0.f;
+            for (int jg = sm.r0; jg < sm.r1; jg += RG) {
+                float pn[NF][RG], pkp[NF][RG], pkm[NF][RG], peu[NF][RG], ped[NF][RG];
+                float2 bdv[RG];
+                float pm0[NF], pc0[NF];
                 const bool need0 = !have;
 #pragma unroll
-                for (int q = 0; q < kRowGroup; ++q) {
+                for (int q = 0; q < RG; ++q) {
                     const int jl = jg + q, j = j0 + jl;
-                    pn[q] = pkp[q] = pkm[q] = peu[q] = ped[q] = 0.f;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        pn[f][q] = pkp[f][q] = pkm[f][q] = peu[f][q] = ped[f][q] = 0.f;
+                        if (q == 0) pm0[f] = pc0[f] = 0.f;
+                    }
                     bdv[q] = make_float2(0.f, 0.f);
                     if (jl < sm.r1 && j < ny) {
                         const int jp = (j + 1 == ny) ? 0 : j + 1;
                         const int jm = (j == 0) ? ny - 1 : j - 1;
                         const int row = j * nx;
-                        if (q == 0 && need0) {
-                            pm0 = __ldg(ph + jm * nx + ii);
-                            pc0 = __ldg(ph + row + ii);
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const float *ph = phw[f];
+                            if (q == 0 && need0) {
+                                pm0[f] = __ldg(ph + jm * nx + ii);
+                                pc0[f] = __ldg(ph + row + ii);
+                            }
+                            pn[f][q] = __ldg(ph + jp * nx + ii);
+                            if (k + 1 < nz) pkp[f][q] = __ldg(ph + plane + row + ii);
+                            if (k > 0) pkm[f][q] = __ldg(ph + row + ii - plane);
+                            if (own_up) peu[f][q] = __ldg(ph + row + ip);
+                            if (own_dn) ped[f][q] = __ldg(ph + row + im);
                         }
-                        pn[q] = __ldg(ph + jp * nx + ii);
-                        if (k + 1 < nz) pkp[q] = __ldg(ph + plane + row + ii);
-                        if (k > 0) pkm[q] = __ldg(ph + row + ii - plane);
-                        if (own_up) peu[q] = __ldg(ph + row + ip);
-                        if (own_dn) ped[q] = __ldg(ph + row + im);
                         if (act) bdv[q] = __ldg(bd + row + i);
                     }
                 }
                 if (need0) {
-                    Pm = pm0;
-                    Pc = pc0;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        Pm[f] = pm0[f];
+                        Pc[f] = pc0[f];
+                    }
                 }
                 // two rows at a time: their stencil neighbours gathered as scalars, then the
                 // residual of both in two-lane float-float operations (bit for bit the
                 // scalar sequence); both rows' values go to one FFT slot (x: even row, y: odd)
 #pragma unroll
-                for (int q = 0; q < kRowGroup; q += 2) {
+                for (int q = 0; q < RG; q += 2) {
                     const int jl0 = jg + q;
                     if (jl0 >= sm.r1) break;  // warp-uniform
-                    float xp[2], xm[2], yp[2], ym[2], zp[2], zm[2], pc[2];
+                    float xp[NF][2], xm[NF][2], yp[NF][2], ym[NF][2], zp[NF][2], zm[NF][2], pc[NF][2];
                     bool live[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int j = j0 + jl0 + h;
                         live[h] = jl0 + h < sm.r1 && j < ny;
-                        const float P = Pc;
-                        float Pip = __shfl_down_sync(0xffffffffu, P, 1);
-                        if (own_up) Pip = peu[q + h];
-                        float Pim = __shfl_up_sync(0xffffffffu, P, 1);
-                        if (own_dn) Pim = ped[q + h];
-                        if (wall_x && ii + 1 == nx) Pip = P;
-                        if (wall_x && ii == 0) Pim = P;
-                        float Pjp = pn[q + h], Pjm = Pm;
-                        if (wall_y && j + 1 == ny) Pjp = P;
-                        if (wall_y && j == 0) Pjm = P;
-                        xp[h] = Pip; xm[h] = Pim; yp[h] = Pjp; ym[h] = Pjm; pc[h] = P;
-                        // top: Neumann (difference zero) or Dirichlet outlet (phi = 0 on the face)
-                        zp[h] = (k + 1 < nz) ? pkp[q + h] : (G.dir_top ? 0.f : P);
-                        zm[h] = (k > 0) ? pkm[q + h] : P;
-                        if (live[h]) {
-                            Pm = P;
-                            Pc = pn[q + h];
-                            have = true;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const float P = Pc[f];
+                            float Pip = __shfl_down_sync(0xffffffffu, P, 1);
+                            if (own_up) Pip = peu[f][q + h];
+                            float Pim = __shfl_up_sync(0xffffffffu, P, 1);
+                            if (own_dn) Pim = ped[f][q + h];
+                            if (wall_x && ii + 1 == nx) Pip = P;
+                            if (wall_x && ii == 0) Pim = P;
+                            float Pjp = pn[f][q + h], Pjm = Pm[f];
+                            if (wall_y && j + 1 == ny) Pjp = P;
+                            if (wall_y && j == 0) Pjm = P;
+                            xp[f][h] = Pip; xm[f][h] = Pim; yp[f][h] = Pjp; ym[f][h] = Pjm; pc[f][h] = P;
+                            // top: Neumann (difference zero) or Dirichlet outlet (phi = 0 on the face)
+                            zp[f][h] = (k + 1 < nz) ? pkp[f][q + h] : (G.dir_top ? 0.f : P);
+                            zm[f][h] = (k > 0) ? pkm[f][q + h] : P;
+                            if (live[h]) {
+                                Pm[f] = P;
+                                Pc[f] = pn[f][q + h];
+                            }
+                        }
+                        have = live[h];
+                    }
+                    df2 d2x, d2y, dzp, dzm;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const float2 PC = make_float2(pc[f][0], pc[f][1]);
+                        const float2 NPC = p2mul(PC, make_float2(-1.f, -1.f)), M2 = p2add(NPC, NPC);
+                        const float2 XP = make_float2(xp[f][0], xp[f][1]), XM = make_float2(xm[f][0], xm[f][1]);
+                        const float2 YP = make_float2(yp[f][0], yp[f][1]), YM = make_float2(ym[f][0], ym[f][1]);
+                        const df2 ax = sum3u2(XP, XM, M2);
+                        const df2 ay = sum3u2(YP, YM, M2);
+                        const df2 azp = two_sum2(make_float2(zp[f][0], zp[f][1]), NPC);
+                        const df2 azm = two_sum2(PC, p2mul(make_float2(zm[f][0], zm[f][1]), make_float2(-1.f, -1.f)));
+                        if (f == 0) {
+                            d2x = ax; d2y = ay; dzp = azp; dzm = azm;
                         } else {
-                            have = false;
+                            d2x = df_add2(d2x, ax); d2y = df_add2(d2y, ay);
+                            dzp = df_add2(dzp, azp); dzm = df_add2(dzm, azm);
                         }
                     }
-                    const float2 PC = make_float2(pc[0], pc[1]);
-                    const float2 NPC = p2mul(PC, make_float2(-1.f, -1.f)), M2 = p2add(NPC, NPC);
-                    const df2 d2x = sum3u2(make_float2(xp[0], xp[1]), make_float2(xm[0], xm[1]), M2);
-                    const df2 d2y = sum3u2(make_float2(yp[0], yp[1]), make_float2(ym[0], ym[1]), M2);
-                    const df2 dzp = two_sum2(make_float2(zp[0], zp[1]), NPC);
-                    const df2 dzm = two_sum2(PC, p2mul(make_float2(zm[0], zm[1]), make_float2(-1.f, -1.f)));
                     const df2 bv2 = {make_float2(bdv[q].x, bdv[q + 1].x), make_float2(bdv[q].y, bdv[q + 1].y)};
                     const df2 r = df_resid4_2(bv2, cp, cu, d2x, cv, d2y, cwp, dzp, cwm, dzm);
                     const float2 val = p2mul(p2add(r.hi, r.lo), make_float2(scale, scale));
                     const bool u0 = act && live[0], u1 = act && live[1];
-                    acc2 = df_addf2(acc2, make_float2(u0 ? pc[0] : 0.f, u1 ? pc[1] : 0.f));
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        acc2 = df_addf2(acc2, make_float2(u0 ? pc[f][0] : 0.f, u1 ? pc[f][1] : 0.f));
                     accr = df_add2(accr, df2{make_float2(u0 ? r.hi.x : 0.f, u1 ? r.hi.y : 0.f),
                                              make_float2(u0 ? r.lo.x : 0.f, u1 ? r.lo.y : 0.f)});
                     if (act) {

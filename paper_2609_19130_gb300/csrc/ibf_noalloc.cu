@@ -178,7 +178,8 @@ extern "C" ibf_status ibf_project_noalloc(const ibf_grid *grid, const ibf_opts *
         const size_t fwd = kYZStages * ((d.mb * sstr * csz + nslot * rsz + 15) & ~(size_t)15) + nslot * csz;
         const size_t bwd = kYZStages * ((nslot * (csz + rsz) + 15) & ~(size_t)15) + (d.mb * sstr + nslot) * csz;
         yzsmem = std::max(fwd, bwd);
-        if (mixed && d.mb == 1 && !d.wall_y) yzsmem = std::max(yzsmem, yz_pipe_smem(d.ny, (int)sstr));
+        if (mixed && d.mb == 1 && !d.wall_y)
+            yzsmem = std::max(yzsmem, std::max(yz_pipe_smem(d.ny, (int)sstr), yz_bulk_smem(d.ny, (int)sstr)));
     }
     const size_t smem00 = (size_t)10 * (nz + 1) * 8;
     const size_t cap = smem_cap_of(optin);  // the limit ibf_projection_plan applies

@@ -223,6 +223,273 @@ __device__ void yzbwd_pipe(const Work &w, const GridDev &G, int cb, unsigned cha
     }
 }
 
+// ---------------------------------------------------------------- round-based forms
+// Mixed path, one x-mode per column block, periodic y, even ny (the benchmark's shape).
+// The planes of the column block go in rounds of kBulkPlanes: in round r one thread
+// issues bulk asynchronous copies (cp.async.bulk, completed on an mbarrier per buffer)
+// of round r+1's planes into the other of two buffer sets, while
+//   forward:  warps 0..kBulkPlanes-1 each transform one plane of round r (the warp first
+//             moves its dense copy to the padded FFT layout in place), then all threads run
+//             the Thomas forward step of the round's planes in order, each thread on fixed
+//             slots, the state d'_{k-1} in registers within the round;
+//   backward: all threads back-substitute the round's planes in order (each thread reads
+//             its slots of a plane's dense copy, a barrier, then writes phi_hat in the
+//             padded layout of the same buffer), then warps 0..kBulkPlanes-1 each
+//             inverse-transform one plane and store it.
+// kBulkPlanes FFT warps per CTA and four CTAs per SM keep twelve plane transforms in
+// flight per SM (the one-warp transform of a plane is latency-bound), and the copies of
+// the next round overlap the current one.  Waits on the copies give up after
+// kBulkWaitLimit polls and set IBF_ERR_TIMEOUT.
+constexpr int kBulkSlots = 1024 / kYZThreads;  // slots per thread (ny <= 1024)
+
+// In place, by one warp: the dense plane (element p at p) moved to the padded FFT layout
+// (element p at p + p / N2).  Blocks of 32 elements are moved from the last to the first;
+// every target is at or above its source, and the lanes load a block before any stores
+// it, so nothing is overwritten before it is read.
+__device__ __forceinline__ void spread_dense_to_padded(cx<float> *b, int n, int N2, const FDiv &fN2, int lane) {
+    for (int base = ((n - 1) >> 5) << 5; base >= 0; base -= 32) {
+        const int p = base + lane;
+        cx<float> v;
+        if (p < n) v = b[p];
+        __syncwarp();
+        if (p < n) b[pos_nat(p, fN2)] = v;
+        __syncwarp();
+    }
+}
+
+// After a copy of round r was not seen within the wait limit: report IBF_ERR_TIMEOUT and
+// let the copies of round r+1, already issued, land (bounded) before the CTA exits.
+__device__ __forceinline__ void bulk_lost_cleanup(const Work &w, unsigned long long *bar, int r, int nround, int nz,
+                                                  int tid) {
+    if (tid != 0) return;
+    atomicOr(w.err, 1u << 5);  // IBF_ERR_TIMEOUT
+    if (r + 1 < nround)
+        for (int f = 0; f < kBulkPlanes && (r + 1) * kBulkPlanes + f < nz; ++f)
+            mbar_wait_bounded(bar + ((r + 1) & 1) * kBulkPlanes + f, (unsigned)((r + 1) >> 1) & 1u, kBulkWaitLimit);
+}
+
+// The Thomas forward step of one round's planes (yzfwd_bulk), in a function of its own so
+// that its pointers and the round's loads are not live across the transforms, which need
+// the whole 128-register budget.
+__device__ __noinline__ void yzfwd_bulk_sweep(const Work &w, const GridDev &G, int cb, unsigned char *smem, int r) {
+    const int ny = G.ny, nz = G.nz, ncb = G.ncb;
+    const int sstride = fft_seq_len(G.ny1, G.ny2) + 1;
+    const FDiv fN2 = G.fny2;
+    const size_t sb = pipe_align16((size_t)max(sstride, ny) * 8);
+    auto buf = [&](int set, int f) { return reinterpret_cast<cx<float> *>(smem + (size_t)(set * kBulkPlanes + f) * sb); };
+    cx<float> *specw = reinterpret_cast<cx<float> *>(w.spec) + G.spec_off;
+    const float *tab = reinterpret_cast<const float *>(w.tab) + G.tab_off;
+    const float *az = w.z.azf + G.z_off;
+    const int tid = threadIdx.x;
+    // All of the round's global loads first (the state and the pivots of every
+    // plane), so that the sweep waits for memory once per round.
+    cx<float> st[kBulkSlots];
+    float inv[kBulkPlanes][kBulkSlots];
+#pragma unroll
+    for (int i = 0; i < kBulkSlots; ++i) {
+        const int q = tid + i * kYZThreads;
+        st[i] = (r > 0 && q < ny) ? specw[((size_t)(r * kBulkPlanes - 1) * ncb + cb) * ny + q] : cx<float>{0.f, 0.f};
+    }
+#pragma unroll
+    for (int f = 0; f < kBulkPlanes; ++f) {
+        const int k = min(r * kBulkPlanes + f, nz - 1);
+        const float *t = tab + ((size_t)k * ncb + cb) * ny;
+#pragma unroll
+        for (int i = 0; i < kBulkSlots; ++i) {
+            const int q = tid + i * kYZThreads;
+            inv[f][i] = q < ny ? __ldg(t + q) : 0.f;
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < kBulkPlanes; ++f) {
+        const int k = r * kBulkPlanes + f;
+        if (k < nz) {
+            const cx<float> *b = buf(r & 1, f);
+            cx<float> *pl = specw + ((size_t)k * ncb + cb) * ny;
+            const float a = az[k];
+#pragma unroll
+            for (int i = 0; i < kBulkSlots; ++i) {
+                const int q = tid + i * kYZThreads;
+                if (q < ny) {
+                    const cx<float> rin = b[pos_nat(q, fN2)];
+                    cx<float> d = {(rin.x - a * st[i].x) * inv[f][i], (rin.y - a * st[i].y) * inv[f][i]};
+                    if (cb == 0 && q == 0) d = rin;  // (0,0) mode: solved by k_00
+                    st[i] = d;
+                    pl[q] = d;
+                }
+            }
+        }
+    }
+}
+
+__device__ void yzfwd_bulk(const Work &w, const GridDev &G, int cb, unsigned char *smem) {
+    const int ny = G.ny, nz = G.nz, ncb = G.ncb;
+    const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fny1, fN2 = G.fny2;
+    const size_t sb = pipe_align16((size_t)max(sstride, ny) * 8);
+    auto buf = [&](int set, int f) { return reinterpret_cast<cx<float> *>(smem + (size_t)(set * kBulkPlanes + f) * sb); };
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + 2 * kBulkPlanes * sb);
+    const cx<float> *spec = reinterpret_cast<const cx<float> *>(w.spec) + G.spec_off;
+    const cx<float> *twy = reinterpret_cast<const cx<float> *>(w.twy) + G.twy_off;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nround = (nz + kBulkPlanes - 1) / kBulkPlanes;
+    const unsigned bytes = (unsigned)ny * 8u;
+    if (tid == 0) {
+        for (int i = 0; i < 2 * kBulkPlanes; ++i) mbar_init(bar + i, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int r) {  // thread 0: the planes of round r into set r & 1
+        for (int f = 0; f < kBulkPlanes; ++f) {
+            const int k = r * kBulkPlanes + f;
+            if (k >= nz) break;
+            if (w.fault_lose_copy && r == 1 && f == 0) continue;  // test hook: this copy never arrives
+            unsigned long long *b = bar + (r & 1) * kBulkPlanes + f;
+            mbar_arrive_expect_tx(b, bytes);
+            bulk_g2s(buf(r & 1, f), spec + ((size_t)k * ncb + cb) * ny, bytes, b);
+        }
+    };
+    if (tid == 0) issue(0);
+    bool lost = false;
+    for (int r = 0; r < nround; ++r) {
+        if (tid == 0 && r + 1 < nround) {
+            fence_proxy_async_smem();
+            issue(r + 1);
+        }
+        if (warp < kBulkPlanes) {
+            const int k = r * kBulkPlanes + warp;
+            if (k < nz) {
+                if (mbar_wait_bounded(bar + (r & 1) * kBulkPlanes + warp, (unsigned)(r >> 1) & 1u, kBulkWaitLimit)) {
+                    cx<float> *b = buf(r & 1, warp);
+                    spread_dense_to_padded(b, ny, N2, fN2, lane);
+                    fft1_warp_fwd(b, sstride, N1, N2, fN1, fN2, twy, lane);
+                }
+                else
+                    lost = true;
+            }
+        }
+        // a lost copy stops the column block: the error is reported, nothing more is waited on
+        if (__syncthreads_or(lost)) {
+            bulk_lost_cleanup(w, bar, r, nround, nz, tid);
+            return;
+        }
+        // the sweep reads back, as the Thomas state, what each thread stored for the last
+        // plane of the previous round (rather than holding it across the transforms)
+        yzfwd_bulk_sweep(w, G, cb, smem, r);
+        fence_proxy_async_smem();  // this thread's reads of the set before its next copies
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int i = 0; i < 2 * kBulkPlanes; ++i) mbar_inval(bar + i);
+}
+
+__device__ __noinline__ void fft1_warp_inv_call(cx<float> *buf, int sstride, int N1, int N2, const FDiv fN1,
+                                                const FDiv fN2, const cx<float> *tw, int lane) {
+    fft1_warp_inv(buf, sstride, N1, N2, fN1, fN2, tw, lane);
+}
+
+__device__ void yzbwd_bulk(const Work &w, const GridDev &G, int cb, unsigned char *smem) {
+    const int ny = G.ny, nz = G.nz, ncb = G.ncb;
+    const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
+    const FDiv fN1 = G.fny1, fN2 = G.fny2;
+    const size_t sb = pipe_align16((size_t)max(sstride, ny) * 8);
+    auto buf = [&](int set, int f) { return reinterpret_cast<cx<float> *>(smem + (size_t)(set * kBulkPlanes + f) * sb); };
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + 2 * kBulkPlanes * sb);
+    cx<float> *spec = reinterpret_cast<cx<float> *>(w.spec) + G.spec_off;
+    const float *tab = reinterpret_cast<const float *>(w.tab) + G.tab_off;
+    const cx<float> *twy = reinterpret_cast<const cx<float> *>(w.twy) + G.twy_off;
+    const float *cz = w.z.czf + G.z_off;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nround = (nz + kBulkPlanes - 1) / kBulkPlanes;
+    const unsigned bytes = (unsigned)ny * 8u;
+    if (tid == 0) {
+        for (int i = 0; i < 2 * kBulkPlanes; ++i) mbar_init(bar + i, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int r) {  // planes counted from the top: i = r kBulkPlanes + f -> k = nz - 1 - i
+        for (int f = 0; f < kBulkPlanes; ++f) {
+            const int i = r * kBulkPlanes + f;
+            if (i >= nz) break;
+            const int k = nz - 1 - i;
+            unsigned long long *b = bar + (r & 1) * kBulkPlanes + f;
+            mbar_arrive_expect_tx(b, bytes);
+            bulk_g2s(buf(r & 1, f), spec + ((size_t)k * ncb + cb) * ny, bytes, b);
+        }
+    };
+    if (tid == 0) issue(0);
+    cx<float> st[kBulkSlots];  // phi_hat_{k+1} of this thread's slots
+#pragma unroll
+    for (int i = 0; i < kBulkSlots; ++i) st[i] = {0.f, 0.f};
+    bool lost = false;
+    for (int r = 0; r < nround; ++r) {
+        if (tid == 0 && r + 1 < nround) {
+            fence_proxy_async_smem();
+            issue(r + 1);
+        }
+        // the pivots (times cz_k) of every plane of the round, loaded before any wait
+        float cp[kBulkPlanes][kBulkSlots];
+        float s00[kBulkPlanes];
+#pragma unroll
+        for (int f = 0; f < kBulkPlanes; ++f) {
+            const int k = max(nz - 1 - (r * kBulkPlanes + f), 0);
+            const float *t = tab + ((size_t)k * ncb + cb) * ny;
+            const float c = cz[k];
+#pragma unroll
+            for (int i = 0; i < kBulkSlots; ++i) {
+                const int q = tid + i * kYZThreads;
+                cp[f][i] = q < ny ? c * __ldg(t + q) : 0.f;
+            }
+            s00[f] = (cb == 0 && tid == 0) ? (float)w.sol00[G.z_off + k] : 0.f;
+        }
+#pragma unroll
+        for (int f = 0; f < kBulkPlanes; ++f) {
+            const int i0 = r * kBulkPlanes + f;
+            if (i0 >= nz) break;
+            if (!mbar_wait_bounded(bar + (r & 1) * kBulkPlanes + f, (unsigned)(r >> 1) & 1u, kBulkWaitLimit))
+                lost = true;
+            // a lost copy stops the column block: the error is reported, nothing more is waited on
+            if (__syncthreads_or(lost)) {
+                bulk_lost_cleanup(w, bar, r, nround, nz, tid);
+                return;
+            }
+            cx<float> *b = buf(r & 1, f);
+            cx<float> dv[kBulkSlots];
+#pragma unroll
+            for (int i = 0; i < kBulkSlots; ++i) {
+                const int q = tid + i * kYZThreads;
+                dv[i] = q < ny ? b[q] : cx<float>{0.f, 0.f};
+            }
+            __syncthreads();  // the plane's dense copy is read: its padded layout may be written
+#pragma unroll
+            for (int i = 0; i < kBulkSlots; ++i) {
+                const int q = tid + i * kYZThreads;
+                if (q < ny) {
+                    cx<float> ph = {dv[i].x - cp[f][i] * st[i].x, dv[i].y - cp[f][i] * st[i].y};
+                    if (cb == 0 && q == 0) ph = {s00[f], 0.f};  // (0,0): k_00's solution
+                    st[i] = ph;
+                    b[pos_nat(q, fN2)] = ph;
+                }
+            }
+        }
+        __syncthreads();
+        if (warp < kBulkPlanes) {
+            const int i0 = r * kBulkPlanes + warp;
+            if (i0 < nz) {
+                const int k = nz - 1 - i0;
+                cx<float> *b = buf(r & 1, warp);
+                fft1_warp_inv_call(b, sstride, N1, N2, fN1, fN2, twy, lane);
+                cx<float> *pl = spec + ((size_t)k * ncb + cb) * ny;
+                for (int j = lane; j < ny; j += 32) pl[j] = b[pos_nat(j, fN2)];
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int i = 0; i < 2 * kBulkPlanes; ++i) mbar_inval(bar + i);
+}
+
 // y-FFT + Thomas forward elimination of one column block, sweeping k = 0..nz-1.
 // Shared memory: kYZStages x [FFT buffer (mb padded sequences) | pivot chunk], then the
 // Thomas state d'_{k-1} of every mode of the block.  Plane k+1 (spectrum and pivots)
@@ -237,7 +504,9 @@ __global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 
     const int cb = blockIdx.x - __ldg(w.ystr_start + g);
     if constexpr (sizeof(T) == 4) {
         if (G.mb == 1 && !(W && G.wall_y)) {
-            yzfwd_pipe(w, G, cb, smem_raw);
+            // whole-plane bulk copies need 16-byte aligned planes: even ny and spectrum offset
+            if (((G.ny | (int)G.spec_off) & 1) == 0) yzfwd_bulk(w, G, cb, smem_raw);
+            else yzfwd_pipe(w, G, cb, smem_raw);
             return;
         }
     }
@@ -318,7 +587,8 @@ __global__ void __launch_bounds__(kYZThreads, sizeof(T) == 4 ? kYZResidentF32 : 
     const int cb = blockIdx.x - __ldg(w.ystr_start + g);
     if constexpr (sizeof(T) == 4) {
         if (G.mb == 1 && !(W && G.wall_y)) {
-            yzbwd_pipe(w, G, cb, smem_raw);
+            if (((G.ny | (int)G.spec_off) & 1) == 0) yzbwd_bulk(w, G, cb, smem_raw);
+            else yzbwd_pipe(w, G, cb, smem_raw);
             return;
         }
     }

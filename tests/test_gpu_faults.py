@@ -58,3 +58,29 @@ def test_injected_allocation_failure():
     env = dict(os.environ, IBF_FAULT_OOM_AT="5")
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+def test_lost_copy_reported_as_timeout():
+    """IBF_FAULT_LOSE_COPY makes the round-based forward y/z kernel skip one of its bulk
+    plane copies: the wait for it gives up after its poll limit (no hang, no fault), the
+    column blocks stop, and ibf_plan_sync_status reports IBF_ERR_TIMEOUT; a plan built
+    without the hook in the same process then projects normally."""
+    code = (
+        "import sys, os; sys.path.insert(0, %r)\n"
+        "import torch\n"
+        "from paper_2609_19130_gb300 import Grid, Plan, MIXED, synth, _native as N\n"
+        "g = Grid(64, 32, 12, 1.0, 1.0, 1.0, beta=1.5)\n"
+        "tun = [dict(yz_kernel=1, mb=1)]\n"
+        "u, v, w = (torch.from_numpy(a).cuda() for a in synth.uniform_velocity_np(3, 64, 32, 12))\n"
+        "p = Plan([g], precision=MIXED, refine_steps=1, tuning=tun)\n"
+        "p.project(u, v, w, 1e-3); torch.cuda.synchronize()\n"
+        "st = p.sync_status(); p.close()\n"
+        "assert st == N.IBF_ERR_TIMEOUT, st\n"
+        "os.environ.pop('IBF_FAULT_LOSE_COPY')\n"
+        "q = Plan([g], precision=MIXED, refine_steps=1, tuning=tun)\n"
+        "q.project(u, v, w, 1e-3); torch.cuda.synchronize()\n"
+        "assert q.sync_status() == N.IBF_OK\n"
+        "q.close(); print('ok')\n" % ROOT)
+    env = dict(os.environ, IBF_FAULT_LOSE_COPY="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
