@@ -204,6 +204,11 @@ __device__ __forceinline__ df2 df_add2(df2 a, df2 b) {
     const df2 s = two_sum2(a.hi, b.hi);
     return quick_two_sum2(s.hi, p2add(s.lo, p2add(a.lo, b.lo)));
 }
+// df_sub on two values: lane for lane the scalar df_sub (df_add of the negation)
+__device__ __forceinline__ df2 df_sub2(df2 a, df2 b) {
+    const float2 m = make_float2(-1.f, -1.f);
+    return df_add2(a, df2{p2mul(b.hi, m), p2mul(b.lo, m)});
+}
 // df_dot3 on two values: products per lane, every sum in two-lane operations
 __device__ __forceinline__ df2 df_dot3_2(df c1, df2 d1, df c2, df2 d2, df c3, df2 d3) {
     float2 p1, p2, p3, e1, e2, e3;

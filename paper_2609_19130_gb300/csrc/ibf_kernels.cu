@@ -295,13 +295,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
             // first refinement sweep: phi_0 is plain fp32, so the second differences are
             // exact float sums (a missing wall neighbour is replaced by the cell itself,
             // which zeroes its difference) and only the coefficient products and the
-            // final sums round, at float-float precision.  (Later sweeps, whose phi is
-            // hi + lo, use the general float-float stencil below on purpose: it forms the
-            // second differences from the same float-float first differences as the
-            // velocity correction, so the rounding of those differences is in the residual
-            // the last sweep corrects and cancels in D u.  Exact second differences of each
-            // word, inconsistent with the correction, left max|D u| / max|D u*| at 1.8e-9
-            // at the bench size instead of 7e-12.)
+            // final sums round, at float-float precision.
             constexpr int NF = 1;
             constexpr int RG = NF == 2 ? 2 : kRowGroup;  // rows whose loads go together
             const float *phw[2] = {w.phi_hi + G.cell_off + pbase, w.phi_lo + G.cell_off + pbase};
@@ -426,6 +420,121 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                             if (jl0 + 1 < sm.r1)
                                 *(reinterpret_cast<float *>(buf + ((jl0 + 1) >> 1) * sstride + spos) + ((jl0 + 1) & 1)) = v1;
                         }
+                    }
+                }
+            }
+            acc_phi = df_add(acc_phi, df_add(df{acc2.hi.x, acc2.lo.x}, df{acc2.hi.y, acc2.lo.y}));
+            acc = df_add(acc, df_add(df{accr.hi.x, accr.lo.x}, df{accr.hi.y, accr.lo.y}));
+        } else if constexpr (MODE == XM_RESID && IsDF<A>::value) {
+            // a later refinement sweep: phi = hi + lo (float-float, possibly unnormalised).
+            // The first differences of phi are formed exactly as the velocity correction
+            // forms them (df_sub, lane for lane), so that their rounding is part of the
+            // residual this sweep corrects and cancels in D u; second differences, products
+            // and sums as in the first sweep, two rows at a time in packed operations.
+            const float *phw[2] = {w.phi_hi + G.cell_off + pbase, w.phi_lo + G.cell_off + pbase};
+            const float2 *bd = w.bdf + G.cell_off + pbase;
+            float Pm[2] = {0.f, 0.f}, Pc[2] = {0.f, 0.f};
+            bool have = false;
+            df2 acc2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of phi, per lane
+            df2 accr = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of the residual, per lane
+            constexpr int RG = 2;
+            for (int jg = sm.r0; jg < sm.r1; jg += RG) {
+                float pn[2][RG], pkp[2][RG], pkm[2][RG], peu[2][RG], ped[2][RG];
+                float2 bdv[RG];
+                float pm0[2] = {0.f, 0.f}, pc0[2] = {0.f, 0.f};
+                const bool need0 = !have;
+#pragma unroll
+                for (int q = 0; q < RG; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+#pragma unroll
+                    for (int f = 0; f < 2; ++f) pn[f][q] = pkp[f][q] = pkm[f][q] = peu[f][q] = ped[f][q] = 0.f;
+                    bdv[q] = make_float2(0.f, 0.f);
+                    if (jl < sm.r1 && j < ny) {
+                        const int jp = (j + 1 == ny) ? 0 : j + 1;
+                        const int jm = (j == 0) ? ny - 1 : j - 1;
+                        const int row = j * nx;
+#pragma unroll
+                        for (int f = 0; f < 2; ++f) {
+                            const float *ph = phw[f];
+                            if (q == 0 && need0) {
+                                pm0[f] = __ldg(ph + jm * nx + ii);
+                                pc0[f] = __ldg(ph + row + ii);
+                            }
+                            pn[f][q] = __ldg(ph + jp * nx + ii);
+                            if (k + 1 < nz) pkp[f][q] = __ldg(ph + plane + row + ii);
+                            if (k > 0) pkm[f][q] = __ldg(ph + row + ii - plane);
+                            if (own_up) peu[f][q] = __ldg(ph + row + ip);
+                            if (own_dn) ped[f][q] = __ldg(ph + row + im);
+                        }
+                        if (act) bdv[q] = __ldg(bd + row + i);
+                    }
+                }
+                if (need0) {
+#pragma unroll
+                    for (int f = 0; f < 2; ++f) {
+                        Pm[f] = pm0[f];
+                        Pc[f] = pc0[f];
+                    }
+                }
+                const int jl0 = jg;
+                if (jl0 >= sm.r1) break;  // warp-uniform
+                // the two rows' stencil values as float-float pairs, lanes = rows
+                float xp[2][2], xm[2][2], yp[2][2], ym[2][2], zp[2][2], zm[2][2], pc[2][2];
+                bool live[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = j0 + jl0 + h;
+                    live[h] = jl0 + h < sm.r1 && j < ny;
+#pragma unroll
+                    for (int f = 0; f < 2; ++f) {
+                        const float P = Pc[f];
+                        float Pip = __shfl_down_sync(0xffffffffu, P, 1);
+                        if (own_up) Pip = peu[f][h];
+                        float Pim = __shfl_up_sync(0xffffffffu, P, 1);
+                        if (own_dn) Pim = ped[f][h];
+                        // wall faces carry no gradient: the neighbour is the cell itself,
+                        // whose difference df_sub makes exactly zero
+                        if (wall_x && ii + 1 == nx) Pip = P;
+                        if (wall_x && ii == 0) Pim = P;
+                        float Pjp = pn[f][h], Pjm = Pm[f];
+                        if (wall_y && j + 1 == ny) Pjp = P;
+                        if (wall_y && j == 0) Pjm = P;
+                        xp[f][h] = Pip; xm[f][h] = Pim; yp[f][h] = Pjp; ym[f][h] = Pjm; pc[f][h] = P;
+                        // top: Neumann (difference zero) or Dirichlet outlet (phi = 0 on the face)
+                        zp[f][h] = (k + 1 < nz) ? pkp[f][h] : (G.dir_top ? 0.f : P);
+                        zm[f][h] = (k > 0) ? pkm[f][h] : P;
+                        if (live[h]) {
+                            Pm[f] = P;
+                            Pc[f] = pn[f][h];
+                        }
+                    }
+                    have = live[h];
+                }
+                auto pair = [](const float (&a)[2][2]) {
+                    return df2{make_float2(a[0][0], a[0][1]), make_float2(a[1][0], a[1][1])};
+                };
+                const df2 PC = pair(pc);
+                const df2 d2x = df_sub2(df_sub2(pair(xp), PC), df_sub2(PC, pair(xm)));
+                const df2 d2y = df_sub2(df_sub2(pair(yp), PC), df_sub2(PC, pair(ym)));
+                const df2 dzp = df_sub2(pair(zp), PC);
+                const df2 dzm = df_sub2(PC, pair(zm));
+                const df2 bv2 = {make_float2(bdv[0].x, bdv[1].x), make_float2(bdv[0].y, bdv[1].y)};
+                const df2 r = df_resid4_2(bv2, cp, cu, d2x, cv, d2y, cwp, dzp, cwm, dzm);
+                const float2 val = p2mul(p2add(r.hi, r.lo), make_float2(scale, scale));
+                const bool u0 = act && live[0], u1 = act && live[1];
+                acc2 = df_addf2(acc2, make_float2(u0 ? pc[0][0] : 0.f, u1 ? pc[0][1] : 0.f));
+                acc2 = df_addf2(acc2, make_float2(u0 ? pc[1][0] : 0.f, u1 ? pc[1][1] : 0.f));
+                accr = df_add2(accr, df2{make_float2(u0 ? r.hi.x : 0.f, u1 ? r.hi.y : 0.f),
+                                         make_float2(u0 ? r.lo.x : 0.f, u1 ? r.lo.y : 0.f)});
+                if (act) {
+                    const float v0 = u0 ? val.x : 0.f, v1 = u1 ? val.y : 0.f;
+                    float *slot = reinterpret_cast<float *>(buf + (jl0 >> 1) * sstride + spos);
+                    if ((jl0 & 1) == 0 && jl0 + 1 < sm.r1) {
+                        *reinterpret_cast<float2 *>(slot) = make_float2(v0, v1);
+                    } else {
+                        slot[jl0 & 1] = v0;
+                        if (jl0 + 1 < sm.r1)
+                            *(reinterpret_cast<float *>(buf + ((jl0 + 1) >> 1) * sstride + spos) + ((jl0 + 1) & 1)) = v1;
                     }
                 }
             }
@@ -861,40 +970,51 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? (L2 ? 4 : 5) : 3)
                 // there sees only the one interior cell
                 if (wall_lo) Pim = ADJ ? A::zero() : Pc;
                 const V Pjw = (wall_y && j == 0) ? (ADJ ? A::zero() : Pc) : Pjm;
-                // the differences of phi (L2: of hi + lo, then those of lo2 added)
-                V dxm = A::sub(Pim, Pc), dym = A::sub(Pjw, Pc), dzm = A::sub(pkm[q], Pc);
-                V Pcn = Pc;
+                // L2: the differences of lo2 in fp32 (lo2 is a few 1e-10 of phi), added to
+                // the low word of each correction term, which is then renormalised
+                float dlx = 0.f, dly = 0.f, dlz = 0.f, Lc = 0.f;
                 if constexpr (L2) {
-                    const float Lc = lc[q];
+                    Lc = lc[q];
                     float Lim = __shfl_up_sync(0xffffffffu, Lc, 1);
                     if (own_dn) Lim = led[q];
                     if (wall_lo) Lim = ADJ ? 0.f : Lc;
                     const float Ljw = (wall_y && j == 0) ? (ADJ ? 0.f : Lc) : L2jm;
-                    dxm = df_addf(dxm, __fsub_rn(Lim, Lc));
-                    dym = df_addf(dym, __fsub_rn(Ljw, Lc));
-                    dzm = df_addf(dzm, __fsub_rn(lkm[q], Lc));
-                    Pcn = df_add3(Pc.hi, Pc.lo, Lc);
+                    dlx = __fsub_rn(Lim, Lc);
+                    dly = __fsub_rn(Ljw, Lc);
+                    dlz = __fsub_rn(lkm[q], Lc);
                     L2jm = Lc;
                 }
+                auto term = [&](V c, V d, float dl) {  // c d (+ c dl with lo2), as an fp64 number
+                    V t = A::mul(c, d);
+                    if constexpr (L2) {
+                        t.lo = __fmaf_rn(c.hi, dl, t.lo);
+                        t = quick_two_sum(t.hi, t.lo);
+                    }
+                    return A::store(t);
+                };
+                auto phi_out = [&](V P) {  // phi (L2: hi + lo + lo2, rounded once) as an fp64 number
+                    if constexpr (L2) P.lo = __fadd_rn(P.lo, Lc);
+                    return A::store(A::norm(P));
+                };
                 if (act) {
                     // the correction t is formed in the solve's high precision; the face
                     // value u* + t is one fp64 add (the fp64 pipe is otherwise idle here)
                     const int c = row + i;
-                    uo[j * nxu + i] = ru[q] + A::store(A::mul(cu, dxm));
-                    vo[c] = rv[q] + A::store(A::mul(cv, dym));
+                    uo[j * nxu + i] = ru[q] + term(cu, A::sub(Pim, Pc), dlx);
+                    vo[c] = rv[q] + term(cv, A::sub(Pjw, Pc), dly);
                     if (ADJ) {
-                        wo[c] = rw[q] + A::store(dzm);
-                        if (k == nz - 1) wo[c + plane] = rwt[q] + A::store(A::norm(Pcn));
+                        wo[c] = rw[q] + term(A::from_f(1.f), A::sub(pkm[q], Pc), dlz);
+                        if (k == nz - 1) wo[c + plane] = rwt[q] + phi_out(Pc);
                     } else {
                         if (k == 0) wo[c] = rw[q];
-                        else wo[c] = rw[q] + A::store(A::mul(cw, dzm));
+                        else wo[c] = rw[q] + term(cw, A::sub(pkm[q], Pc), dlz);
                         if (k == nz - 1)  // outlet face: corrected with a Dirichlet outlet, else a wall
-                            wo[c + plane] = G.dir_top ? rwt[q] + A::store(A::mul(cwt, Pcn)) : rwt[q];
+                            wo[c + plane] = G.dir_top ? rwt[q] + term(cwt, Pc, Lc) : rwt[q];
                         if (po) {
                             if constexpr (!PU) {
-                                po[c] = A::store(A::norm(Pcn));
+                                po[c] = phi_out(Pc);
                             } else {
-                                double pv = pn[c] + A::store(A::norm(Pcn));
+                                double pv = pn[c] + phi_out(Pc);
                                 if (pmode == 2) {
                                     double bb;
                                     if constexpr (MIX) {
