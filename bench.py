@@ -224,15 +224,19 @@ def chunked_copy(dst, src, chunk_bytes):
         d[a:a + n].copy_(s_[a:a + n], non_blocking=True)
 
 
-def host_link_rates(h_up, h_down, d_up, d_down):
-    """Pinned host <-> device copy rates in GB/s: one field up alone, one down alone, and
-    both at once on two streams (CUDA events; best of three)."""
+def host_link_rates(h_in, h_out, d_in, d_out):
+    """Pinned host <-> device copy times for one step's traffic, measured in the same
+    process right after the end-to-end run: all input fields up alone, all output fields
+    down alone, and both directions at once on two streams (CUDA events; three repeats,
+    median and best).  The host side of the link is shared, so these rates move from run to
+    run; taking them beside the end-to-end number is what makes the two comparable."""
     import torch
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-    nb_up, nb_down = h_up.numel() * 8, h_down.numel() * 8
+    nb_up = sum(t.numel() * t.element_size() for t in h_in)
+    nb_down = sum(t.numel() * t.element_size() for t in h_out)
 
     def timed(fn):
-        best = None
+        ts = []
         for _ in range(3):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -244,24 +248,31 @@ def host_link_rates(h_up, h_down, d_up, d_down):
             torch.cuda.current_stream().wait_stream(s2)
             e1.record()
             torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) * 1e-3
-            best = t if best is None else min(best, t)
-        return best
+            ts.append(e0.elapsed_time(e1))
+        ts.sort()
+        return ts[1], ts[0]
 
     def up():
         with torch.cuda.stream(s1):
-            d_up.copy_(h_up, non_blocking=True)
+            for d, h in zip(d_in, h_in):
+                d.copy_(h, non_blocking=True)
 
     def down():
         with torch.cuda.stream(s2):
-            h_down.copy_(d_down, non_blocking=True)
+            for h, d in zip(h_out, d_out):
+                h.copy_(d, non_blocking=True)
 
     def both():
         up()
         down()
 
-    return {"h2d_gbs": nb_up / timed(up) / 1e9, "d2h_gbs": nb_down / timed(down) / 1e9,
-            "both_gbs": (nb_up + nb_down) / timed(both) / 1e9, "bytes_each": [nb_up, nb_down]}
+    (u_med, u_best), (d_med, d_best), (b_med, b_best) = timed(up), timed(down), timed(both)
+    return {"h2d_ms": u_med, "d2h_ms": d_med, "both_ms": b_med,
+            "h2d_gbs": nb_up / u_med / 1e6, "d2h_gbs": nb_down / d_med / 1e6,
+            "both_gbs": (nb_up + nb_down) / b_med / 1e6,
+            "best_ms": {"h2d": u_best, "d2h": d_best, "both": b_best},
+            "repeats": 3, "statistic": "median",
+            "bytes": [nb_up, nb_down]}
 
 
 def time_steps(plan, ins, outs, K, W, ws, flush=None):
@@ -705,8 +716,8 @@ def main():
         dev_sets = [(ins, outs), (tuple(torch.empty_like(t) for t in ins), tuple(torch.empty_like(t) for t in outs))]
         h_in = [t.cpu().pin_memory() for t in ins]
         h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
-        s_comp = torch.cuda.current_stream()
-        s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+        s_comp, s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        s_comp.wait_stream(torch.cuda.current_stream())
         h2d = sum(t.numel() * 8 for t in h_in)
         d2h = sum(t.numel() * 8 for t in h_out)
 
@@ -755,14 +766,14 @@ def main():
         e1.record(s_comp)
         torch.cuda.synchronize()
         ems = max_over_ranks(e0.elapsed_time(e1) / ke, ws)
+        link = host_link_rates(h_in, h_out, dev_sets[1][0], dev_sets[1][1])
         line["e2e"] = {"value": ws * cells / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ke,
                        "pipelined": "upload of step i+1 and download of step i overlap step i's projection",
-                       "copy_chunk_mb": args.e2e_chunk_mb or None,
-                       "link": host_link_rates(h_in[0], h_out[0], dev_sets[1][0][0], dev_sets[1][1][0])}
-        lk = line["e2e"]["link"]
-        line["e2e"]["link_bound_ms"] = max(h2d / lk["h2d_gbs"], d2h / lk["d2h_gbs"],
-                                           (h2d + d2h) / lk["both_gbs"]) / 1e6
+                       "copy_chunk_mb": args.e2e_chunk_mb or None, "link": link,
+                       # the link alone, in the better of its two schedules: the directions one
+                       # after the other, or both at once
+                       "link_bound_ms": min(link["h2d_ms"] + link["d2h_ms"], link["both_ms"])}
         line["gpu_launches"] += int(round(launches_per_step * ke))
         del dev_sets, h_in, h_out
 
