@@ -95,12 +95,13 @@ def fp64_peak():
 
 
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of each
-# kernel from one ncu capture (512x512x128 mixed, see profiles/), valid while the
-# kernel sources hash to SOURCES_SHA256; otherwise the roofline's traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.47, "x_forward_residual": 15.27, "correct": 65.24,
-                          "yz_forward": 8.41, "yz_backward": 8.41, "x_inverse_store": 6.55,
-                          "x_inverse_accumulate": 6.56}
-NCU_SOURCES_SHA256 = "6c9d23051839a39f939bcafe5eac12aa66e17e407f3d0a5e50361f0b40a8d247"
+# kernel from one ncu capture (512x512x128 mixed, two refinement sweeps, see profiles/),
+# valid while the kernel sources hash to NCU_SOURCES_SHA256; otherwise the roofline's
+# traffic is null.
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.46, "x_forward_residual": 15.29, "x_forward_residual2": 19.62,
+                          "correct": 69.95, "yz_forward": 8.42, "yz_backward": 8.39, "x_inverse_store": 6.55,
+                          "x_inverse_accumulate": 6.57, "x_inverse_last": 6.56}
+NCU_SOURCES_SHA256 = "99245cf58dc0f808d550620971c054af74987a69b99c55688c13a2cdb1988224"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
                   "ibf_internal.h", "ibf_viscous.h")
 # the same for the viscous solve's kernels (mixed path)
@@ -538,6 +539,42 @@ def bench_batch64(args):
     return 0
 
 
+PROBE_OPS = ("dfma", "dadd", "ffma", "f64_f32_f64_roundtrip_pair", "u32_to_f32_plus_xor_pair", "iadd_plus_xor_pair")
+
+
+def probe_rates():
+    """Instruction rates of this device (libibf_probe.so, Gop/s device-wide and per SM per
+    clock at the SM clock read before and after), as one JSON line."""
+    import ctypes
+    import torch
+    from paper_2609_19130_gb300 import build as B
+    B.build()
+    lib = ctypes.CDLL(B.PROBE_LIB)
+    n = len(PROBE_OPS)
+    buf = (ctypes.c_double * n)()
+    lib.ibfprobe_op_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    clk0 = sm_clock_mhz()
+    rc = lib.ibfprobe_op_rates(buf, n)
+    clk1 = sm_clock_mhz()
+    props = torch.cuda.get_device_properties(0)
+    mhz = max(clk0 or 0, clk1 or 0) or None
+    out = {"device": props.name, "sms": props.multi_processor_count, "status": rc, "sm_mhz": [clk0, clk1],
+           "gops": {k: buf[i] for i, k in enumerate(PROBE_OPS)}}
+    if mhz:
+        out["per_sm_per_clk"] = {k: buf[i] * 1e3 / (props.multi_processor_count * mhz) for i, k in enumerate(PROBE_OPS)}
+    print(json.dumps(out))
+    return rc
+
+
+def sm_clock_mhz():
+    try:
+        r = subprocess.run(["nvidia-smi", "--query-gpu=clocks.sm", "--format=csv,noheader,nounits", "-i", "0"],
+                           capture_output=True, text=True, timeout=20)
+        return float(r.stdout.strip().splitlines()[0])
+    except Exception:
+        return None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -565,6 +602,8 @@ def main():
     ap.add_argument("--batch64", action="store_true", help="time the 64-grid batched workload alone")
     ap.add_argument("--no-batch64", action="store_true", help="skip the 64-grid batched measurement")
     ap.add_argument("--no-autotune-batch", action="store_true", help="default launch shapes for the 64 grids")
+    ap.add_argument("--probe-rates", action="store_true",
+                    help="print the instruction rates measured by libibf_probe.so as one JSON line and exit")
     ap.add_argument("--cpu-child", default="", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -575,6 +614,8 @@ def main():
         return reference_arm(args)
     if args.batch64:
         return bench_batch64(args)
+    if args.probe_rates:
+        return probe_rates()
     if args.warmup < 3:
         args.warmup = 3
 
