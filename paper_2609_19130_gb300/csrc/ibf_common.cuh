@@ -79,7 +79,8 @@ template <> struct Coef<F64Arith> {
     __device__ __forceinline__ static double c2(float2 v, double x) { return x; }
 };
 template <> struct Coef<DFArith> {
-    __device__ __forceinline__ static df c(double x) { return f64_to_df(x); }
+    // per-CTA constants: the general conversion, in line (no call in the kernel's prologue)
+    __device__ __forceinline__ static df c(double x) { return f64_to_df_general(x); }
     __device__ __forceinline__ static df c2(float2 v, double) { return {v.x, v.y}; }
 };
 

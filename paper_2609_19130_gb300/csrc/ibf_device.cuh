@@ -253,8 +253,9 @@ __device__ __forceinline__ df2 df_resid4_2(df2 b, df c0, df c1, df2 d1, df c2, d
 // top 23 fraction bits (truncated); lo = x - hi is formed from the remaining 29
 // bits (rounded to 24 by the integer->float conversion), so hi + lo == x within
 // 2^-48 relative.  |x| < 2^-74 loses lo, |x| < 2^-126 flushes to 0, |x| >= 2^128
-// maps to +-inf, NaN stays NaN.
-__device__ __forceinline__ df f64_to_df(double x) {
+// maps to +-inf, NaN stays NaN.  The general routine; f64_to_df below takes a shorter
+// path for the common exponents and calls this one (out of line) for the rest.
+__device__ __forceinline__ df f64_to_df_general(double x) {
     const unsigned long long X = (unsigned long long)__double_as_longlong(x);
     const unsigned h = (unsigned)(X >> 32), l = (unsigned)X;
     const unsigned e = (h >> 20) & 0x7FFu;
@@ -280,8 +281,9 @@ __device__ __forceinline__ df f64_to_df(double x) {
 // suffices); the only binade change possible is a borrow below a power of two (hi's
 // fraction zero, lo of opposite sign), where the ulp halves.  lo bits below 2^-52 of
 // hi are truncated, a subnormal lo (|hi| below 2^-102) is dropped.  hi zero or
-// subnormal gives a signed zero; hi inf / nan stays inf / nan.
-__device__ __forceinline__ double df_to_f64(df a) {
+// subnormal gives a signed zero; hi inf / nan stays inf / nan.  The general routine;
+// df_to_f64 below takes a shorter path for the common case.
+__device__ __forceinline__ double df_to_f64_general(df a) {
     const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
     const unsigned ha = hb & 0x7FFFFFFFu, sgn = hb & 0x80000000u;
     const bool special = ha >= 0x7F800000u;
@@ -301,12 +303,50 @@ __device__ __forceinline__ double df_to_f64(df a) {
     return __longlong_as_double((long long)H);
 }
 
+static __device__ __noinline__ df f64_to_df_slow(double x) { return f64_to_df_general(x); }
+static __device__ __noinline__ double df_to_f64_slow(df a) { return df_to_f64_general(a); }
+
+// fp64 -> df32, the same result as f64_to_df_general.  Exponents 949..1150 (|x| in
+// [2^-74, 2^128)), where neither part is flushed nor overflows, take the short path:
+// hi is x truncated to 24 bits, and the weight of the 29 remaining fraction bits' unit
+// (x's fp64 ulp) is read off hi's exponent field, 52 binades below it.  Everything else
+// goes to the general routine, out of line, so that the common path carries no
+// special-case selects.
+__device__ __forceinline__ df f64_to_df(double x) {
+    const unsigned long long X = (unsigned long long)__double_as_longlong(x);
+    const unsigned h = (unsigned)(X >> 32), l = (unsigned)X;
+    const unsigned ha = h & 0x7FFFFFFFu;
+    if (ha - (949u << 20) >= ((1151u - 949u) << 20)) return f64_to_df_slow(x);
+    const unsigned hb = __funnelshift_l(l, ha - (896u << 20), 3) | (h & 0x80000000u);
+    const float scale = __uint_as_float((hb & 0xFF800000u) - (52u << 23));
+    return {__uint_as_float(hb), __fmul_rn(__uint2float_rn(l & 0x1FFFFFFFu), scale)};
+}
+
+// df32 -> fp64 for a normalised pair, the same value as df_to_f64_general.  Short path
+// when hi is normal with exponent field 52..254 and a nonzero fraction (so that hi + lo
+// stays in hi's binade): lo, times a power of two that carries hi's sign and makes hi's
+// fp64 ulp the unit, is exactly a float below 2^29 in magnitude; its truncation toward
+// zero is the number of fp64 ulps to add to hi's fp64 bit pattern (hi's own pattern has
+// 29 zero low bits, so the sum never carries out of them or borrows past them).  Other
+// pairs (zero, tiny, huge, special, or hi a power of two) take the general routine.
+__device__ __forceinline__ double df_to_f64(df a) {
+    const unsigned hb = __float_as_uint(a.hi);
+    const unsigned ef = hb & 0x7F800000u;
+    if (ef - (52u << 23) >= ((254u - 52u + 1u) << 23) || (hb & 0x7FFFFFu) == 0u) return df_to_f64_slow(a);
+    const unsigned hw = ((unsigned)((int)hb >> 3) & 0x8FFFFFFFu) + 0x38000000u;
+    const float sc = __uint_as_float(((306u << 23) - ef) | (hb & 0x80000000u));
+    const long long li = (long long)__float2int_rz(__fmul_rn(a.lo, sc));
+    const unsigned long long H = (((unsigned long long)hw << 32) | (unsigned long long)(hb << 29)) + (unsigned long long)li;
+    return __longlong_as_double((long long)H);
+}
+
 // ------------------------------------------------------------------ precision policies
 // FP64 path: everything in double.  MIXED path: transforms in float, stencils in df32.
 struct F64Arith {
     typedef double V;      // high-precision value
     __device__ __forceinline__ static V load(double x) { return x; }
     __device__ __forceinline__ static double store(V v) { return v; }
+    __device__ __forceinline__ static double store_once(V v) { return v; }
     __device__ __forceinline__ static V add(V a, V b) { return a + b; }
     __device__ __forceinline__ static V sub(V a, V b) { return a - b; }
     __device__ __forceinline__ static V mul(V a, V b) { return a * b; }
@@ -318,6 +358,8 @@ struct DFArith {
     typedef df V;
     __device__ __forceinline__ static V load(double x) { return f64_to_df(x); }
     __device__ __forceinline__ static double store(V v) { return df_to_f64(v); }
+    // a value stored once per CTA (a block sum): the general conversion, in line
+    __device__ __forceinline__ static double store_once(V v) { return df_to_f64_general(v); }
     __device__ __forceinline__ static V add(V a, V b) { return df_add(a, b); }
     __device__ __forceinline__ static V sub(V a, V b) { return df_sub(a, b); }
     __device__ __forceinline__ static V mul(V a, V b) { return df_mul(a, b); }

@@ -625,11 +625,11 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
     const int pslot = G.part_off + (k * nrb + rb) * SPLIT + half;
     if (MODE != XM_COPY) {
         V tot = Red<A>::sum(acc, red);
-        if (threadIdx.x == 0) w.partial[pslot] = A::store(tot);
+        if (threadIdx.x == 0) w.partial[pslot] = A::store_once(tot);
     }
     if (MODE == XM_RESID || MODE == XM_RESID0) {
         V totp = Red<A>::sum(acc_phi, red);
-        if (threadIdx.x == 0) w.partial_phi[pslot] = A::store(totp);
+        if (threadIdx.x == 0) w.partial_phi[pslot] = A::store_once(totp);
     }
     if (DIVL) {
         float mx = block_max(vmax, redf);
