@@ -947,6 +947,74 @@ __global__ void __launch_bounds__(kSweepThreads) k_zsweep(Work w) {
     }
 }
 
+// ================================================================ k_plane_sums
+// The plane sums of the right-hand side (and, in a refinement pass, of phi) for k_00:
+// the forward x kernels leave one slot per row block (two with the half-block CTAs); one
+// warp per plane adds its slots, lane-strided then by a butterfly of shuffles (a fixed
+// order), and stores the sum in the plane's first slot, the only one k_00 reads.  Spread
+// over many SMs, since the fp64 pipe of one SM would take the whole sum tens of
+// microseconds.
+constexpr int kPlaneSumThreads = 256;
+__global__ void __launch_bounds__(kPlaneSumThreads) k_plane_sums(Work w, int first_solve) {
+    const GridDev &G = w.grids[blockIdx.y];
+    const int k = blockIdx.x * (kPlaneSumThreads / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (k >= G.nz) return;  // warp-uniform
+    const int np = G.nrb * (w.xfwd_split ? 2 : 1);
+    double *pk = w.partial + G.part_off + (size_t)k * np, *qk = w.partial_phi + G.part_off + (size_t)k * np;
+    double S = 0.0, P = 0.0;
+    for (int r = lane; r < np; r += 32) {
+        S += pk[r];
+        if (!first_solve) P += qk[r];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, o);
+        if (!first_solve) P += __shfl_xor_sync(0xffffffffu, P, o);
+    }
+    // every lane's loads are done (the shuffles consumed them) and only lane 0 read slot 0
+    if (lane == 0) {
+        pk[0] = S;
+        if (!first_solve) qk[0] = P;
+    }
+}
+
+// In-place inclusive prefix sums of a[0..n) in fp64 (rev: suffix sums, a[i] = sum over
+// j >= i), all threads of the block: each thread scans a contiguous chunk, the chunk totals
+// are scanned by warp shuffles and across warps through wsum[blockDim / 32]; a fixed order.
+__device__ void block_scan_fp64(double *a, int n, bool rev, double *wsum) {
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = T >> 5;
+    const int per = (n + T - 1) / T, b0 = min(n, t * per), b1 = min(n, b0 + per);
+    auto at = [&](int i) -> double & { return a[rev ? n - 1 - i : i]; };
+    double loc = 0.0;
+    for (int i = b0; i < b1; ++i) {
+        loc += at(i);
+        at(i) = loc;
+    }
+    double x = loc;  // inclusive scan of the chunk totals within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    double ex = __shfl_up_sync(0xffffffffu, x, 1);  // exclusive: the chunks before this one
+    if (lane == 0) ex = 0.0;
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        double v = lane < nw ? wsum[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < nw) wsum[lane] = v;
+    }
+    __syncthreads();
+    const double off = wid > 0 ? ex + wsum[wid - 1] : ex;
+    for (int i = b0; i < b1; ++i) at(i) += off;
+    __syncthreads();
+}
+
 // ================================================================ k_00 (fp64, one CTA per grid)
 template <typename T>
 __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
@@ -966,21 +1034,18 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     double *Pk = A1;  // plane means of the phi being refined
     double loc = 0.0, locp = 0.0;
     bool bad = false;
-    // np slots per plane (one per row block, two with the half-block forward x-FFT CTAs),
-    // summed in order by one thread per plane (fp64 adds are scarce here: no shuffle tree)
+    // plane sums: k_plane_sums left each plane's in its first slot
     const int np = nrb * (w.xfwd_split ? 2 : 1);
+    double lmax = 0.0;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-        double S = 0.0;
-        for (int r = 0; r < np; ++r) S += part[k * np + r];
-        const double m = S * G.inv_nxy;  // plane mean of b (first solve) or of the residual
+        const double m = part[(size_t)k * np] * G.inv_nxy;  // plane mean of b (first solve) or of the residual
         if (!isfinite(m)) bad = true;
         const double h = w.z.hz[zo + k];
         rhs[k] = m;
         hz[k] = h;
+        lmax = fmax(lmax, fabs(m));
         if (!first_solve) {
-            double P = 0.0;
-            for (int r = 0; r < np; ++r) P += partp[k * np + r];
-            Pk[k] = P * G.inv_nxy;
+            Pk[k] = partp[(size_t)k * np] * G.inv_nxy;
             locp += h * Pk[k];
         }
     }
@@ -1000,12 +1065,20 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     if (threadIdx.x == 0) red[0] = G.dir_top ? 0.0 : tot / G.sum_hz;
     __syncthreads();
     const double mean = red[0];
-    if (threadIdx.x == 0 && first_solve) {
-        w.mean_b[g] = mean;
-        double scale = 0.0;
-        for (int k = 0; k < nz; ++k) scale = fmax(scale, fabs(rhs[k]));
-        // compatibility defect large compared with the plane means -> warning
-        if (fabs(mean) > 1e-8 * scale && fabs(mean) > 0.0) atomicOr(w.err, 1u << 7);
+    if (first_solve) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        __syncthreads();  // red[0] (the mean) has been read by every thread
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            w.mean_b[g] = mean;
+            double scale = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) scale = fmax(scale, red[i]);
+            // compatibility defect large compared with the plane means -> warning
+            if (fabs(mean) > 1e-8 * scale && fabs(mean) > 0.0) atomicOr(w.err, 1u << 7);
+        }
+        __syncthreads();
     }
     // The (0,0) system in flux form.  Row k of L along z, times hz_k, is a difference of
     // face fluxes, hz_k (L phi)_k = F_{k+1/2} - F_{k-1/2} with F_{k+1/2} =
@@ -1018,28 +1091,17 @@ __global__ void __launch_bounds__(256) k_00(Work w, int first_solve) {
     // fixes phi_{nz-1}.  The two running sums are the exact solve of the system; unlike
     // an elimination on the rows a_k, -(a_k + c_k), c_k (whose reduced diagonals cancel
     // by orders of magnitude on a stretched grid) they leave a residual at the rounding
-    // of the fluxes.  Sums in one thread, the divisions by 1/gz in parallel.
-    double *S = B0, *inc = C0;
+    // of the fluxes.  The running sums are block-wide scans (a fixed order), the
+    // divisions by 1/gz are parallel.
+    double *S = A0, *inc = C0;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) A0[k] = hz[k] * (rhs[k] - mean);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double acc = 0.0;
-        for (int k = 0; k < nz; ++k) {
-            acc += A0[k];
-            S[k] = acc;
-        }
-    }
-    __syncthreads();
+    block_scan_fp64(S, nz, false, red);  // S_k, in place
     for (int k = threadIdx.x; k + 1 < nz; k += blockDim.x) inc[k] = S[k] / w.z.rgzf[zo + k + 1];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double ph = G.dir_top ? -S[nz - 1] / (hz[nz - 1] * G.ez_top) : 0.0;
-        D0[nz - 1] = ph;
-        for (int k = nz - 2; k >= 0; --k) {
-            ph -= inc[k];
-            D0[k] = ph;
-        }
-    }
+    block_scan_fp64(inc, nz - 1, true, red);  // inc[k] = sum_{j = k}^{nz-2} gz_{j+1} S_j
+    const double ph_top = G.dir_top ? -S[nz - 1] / (hz[nz - 1] * G.ez_top) : 0.0;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) D0[k] = k + 1 < nz ? ph_top - inc[k] : ph_top;
     __syncthreads();
     double lsv = 0.0;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
@@ -1195,6 +1257,8 @@ cudaError_t launch_yzbwd(int mixed, const Work &w, int nblk, size_t smem, cudaSt
 
 cudaError_t launch_k00(const Work &w, int mixed, int first_solve, int maxnz, cudaStream_t st) {
     const size_t smem = (size_t)10 * (maxnz + 1) * sizeof(double);
+    const int wpb = kPlaneSumThreads / 32;
+    k_plane_sums<<<dim3((unsigned)((maxnz + wpb - 1) / wpb), (unsigned)w.ngrids), kPlaneSumThreads, 0, st>>>(w, first_solve);
     if (mixed) k_00<float><<<w.ngrids, 256, smem, st>>>(w, first_solve);
     else k_00<double><<<w.ngrids, 256, smem, st>>>(w, first_solve);
     return cudaGetLastError();
