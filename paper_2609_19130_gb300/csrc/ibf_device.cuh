@@ -204,10 +204,24 @@ __device__ __forceinline__ df2 df_add2(df2 a, df2 b) {
     const df2 s = two_sum2(a.hi, b.hi);
     return quick_two_sum2(s.hi, p2add(s.lo, p2add(a.lo, b.lo)));
 }
-// df_sub on two values: lane for lane the scalar df_sub (df_add of the negation)
+// df_sub on two values: lane for lane the scalar df_sub (df_add of the negation).  The
+// negation is folded into the subtractions: with round-to-nearest, x + (-y) and
+// -(y + z) round exactly as x - y and the negated sum.
 __device__ __forceinline__ df2 df_sub2(df2 a, df2 b) {
-    const float2 m = make_float2(-1.f, -1.f);
-    return df_add2(a, df2{p2mul(b.hi, m), p2mul(b.lo, m)});
+    const float2 s = p2sub(a.hi, b.hi), bb = p2sub(s, a.hi);
+    const float2 e = p2sub(p2sub(a.hi, p2sub(s, bb)), p2add(b.hi, bb));
+    return quick_two_sum2(s, p2add(e, p2sub(a.lo, b.lo)));
+}
+// df_mul of one float-float c by two values: lane for lane the scalar df_mul(c, d) (the
+// leading product formed negated, which rounds as its negation)
+__device__ __forceinline__ df2 df_mul2(df c, df2 d) {
+    const float2 ch = make_float2(c.hi, c.hi), cl = make_float2(c.lo, c.lo);
+    const float2 pn = p2mul(make_float2(-c.hi, -c.hi), d.hi);
+    float2 e = __ffma2_rn(ch, d.hi, pn);
+    e = __ffma2_rn(ch, d.lo, e);
+    e = __ffma2_rn(cl, d.hi, e);
+    const float2 s = p2sub(e, pn);                 // p + e
+    return {s, p2sub(e, p2add(s, pn))};            // e - (s - p)
 }
 // df_dot3 on two values: products per lane, every sum in two-lane operations
 __device__ __forceinline__ df2 df_dot3_2(df c1, df2 d1, df c2, df2 d2, df c3, df2 d3) {

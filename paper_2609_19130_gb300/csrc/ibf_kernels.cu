@@ -958,6 +958,84 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? (L2 ? 4 : 5) : 3)
                 Pjm = pjm0;
                 L2jm = ljm0;
             }
+            if constexpr (MIX && !ADJ && !PU) {
+                // forward, mixed: both rows of the group at once, row jg in the x lane and row
+                // jg + 1 in the y lane of packed operations (lane for lane the scalar sequence
+                // of the general branch below); the neighbours and the fp64 conversions and
+                // stores per row
+                static_assert(kRowGroupC == 2, "two rows per packed step");
+                bool live[2];
+                df Pcs[2], Pims[2], Pjws[2];
+                float Lcs[2], dlx[2], dly[2], dlz[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = j0 + jg + h;
+                    live[h] = jg + h < sm.r1 && j < ny;
+                    const df Pc = pc[h];
+                    df Pim = shup(Pc, 1);
+                    if (own_dn) Pim = ped[h];
+                    if (wall_lo) Pim = Pc;
+                    const df Pjm_h = h == 0 ? Pjm : pc[0];
+                    Pcs[h] = Pc;
+                    Pims[h] = Pim;
+                    Pjws[h] = (wall_y && j == 0) ? Pc : Pjm_h;
+                    Lcs[h] = dlx[h] = dly[h] = dlz[h] = 0.f;
+                    if constexpr (L2) {
+                        const float Lc = lc[h];
+                        float Lim = __shfl_up_sync(0xffffffffu, Lc, 1);
+                        if (own_dn) Lim = led[h];
+                        if (wall_lo) Lim = Lc;
+                        const float Ljm_h = h == 0 ? L2jm : lc[0];
+                        const float Ljw = (wall_y && j == 0) ? Lc : Ljm_h;
+                        Lcs[h] = Lc;
+                        dlx[h] = __fsub_rn(Lim, Lc);
+                        dly[h] = __fsub_rn(Ljw, Lc);
+                        dlz[h] = __fsub_rn(lkm[h], Lc);
+                    }
+                }
+                if (live[0]) {
+                    auto pk = [](const df (&v)[2]) {
+                        return df2{make_float2(v[0].hi, v[1].hi), make_float2(v[0].lo, v[1].lo)};
+                    };
+                    auto pkf = [](const float (&v)[2]) { return make_float2(v[0], v[1]); };
+                    const df2 P = pk(Pcs);
+                    const df2 ZM = {make_float2(pkm[0].hi, pkm[1].hi), make_float2(pkm[0].lo, pkm[1].lo)};
+                    auto term2 = [&](df c, df2 d, float2 dl) {  // c d (+ c dl with lo2)
+                        df2 t = df_mul2(c, d);
+                        if constexpr (L2) {
+                            t.lo = __ffma2_rn(make_float2(c.hi, c.hi), dl, t.lo);
+                            t = quick_two_sum2(t.hi, t.lo);
+                        }
+                        return t;
+                    };
+                    const df2 tx = term2(cu, df_sub2(pk(Pims), P), pkf(dlx));
+                    const df2 ty = term2(cv, df_sub2(pk(Pjws), P), pkf(dly));
+                    const df2 tz = term2(cw, df_sub2(ZM, P), pkf(dlz));
+                    df2 tt = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    if (k == nz - 1 && G.dir_top) tt = term2(cwt, P, pkf(Lcs));
+                    df2 Pn = P;
+                    if constexpr (L2) Pn.lo = p2add(P.lo, pkf(Lcs));
+                    Pn = quick_two_sum2(Pn.hi, Pn.lo);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (!live[h] || !act) continue;
+                        const int j = j0 + jg + h, c = j * nx + i;
+                        auto lane_of = [h](const df2 &v) {
+                            return h == 0 ? df{v.hi.x, v.lo.x} : df{v.hi.y, v.lo.y};
+                        };
+                        uo[j * nxu + i] = ru[h] + df_to_f64(lane_of(tx));
+                        vo[c] = rv[h] + df_to_f64(lane_of(ty));
+                        if (k == 0) wo[c] = rw[h];
+                        else wo[c] = rw[h] + df_to_f64(lane_of(tz));
+                        if (k == nz - 1)  // outlet face: corrected with a Dirichlet outlet, else a wall
+                            wo[c + plane] = G.dir_top ? rwt[h] + df_to_f64(lane_of(tt)) : rwt[h];
+                        if (po) po[c] = df_to_f64(lane_of(Pn));
+                    }
+                    Pjm = live[1] ? Pcs[1] : Pcs[0];
+                    L2jm = live[1] ? Lcs[1] : Lcs[0];
+                    have = true;
+                }
+            } else {
 #pragma unroll
             for (int q = 0; q < kRowGroupC; ++q) {
                 const int jl = jg + q, j = j0 + jl;
@@ -1032,6 +1110,7 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? (L2 ? 4 : 5) : 3)
                 }
                 Pjm = Pc;
                 have = true;
+            }
             }
         }
     }
