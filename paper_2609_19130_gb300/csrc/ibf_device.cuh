@@ -617,6 +617,33 @@ __device__ __forceinline__ void fft_row_pass(cx<T> *buf, int nseq, int sstride, 
     }
 }
 
+// One warp, one sequence whose input arrives dense (row stride N2, as a contiguous copy
+// leaves it): the column pass reads that layout and writes its outputs to the padded one
+// (row stride N2 + 1) in the same buffer.  One column task per lane (N2 <= 32), and every
+// lane's reads come before any lane's writes (a __syncwarp between), so the in-place
+// change of layout is safe; the row pass then runs on the padded layout as usual.
+template <typename T, int P, int DIR>
+__device__ __forceinline__ void fft_col_task_dense_in(cx<T> *seq, int c, bool active, int N2, const cx<T> *tw) {
+    cx<T> x[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) x[r] = active ? seq[r * N2 + c] : cx<T>{(T)0, (T)0};
+    __syncwarp();
+    if (!active) return;
+    IPDFT<T, P, P, 0, 1, DIR>::run(x);
+    if (DIR < 0 && c > 0) ip_store<T, P, 0, true, false>(x, seq + c, N2 + 1, tw + c, N2);
+    else ip_store<T, P, 0, false, false>(x, seq + c, N2 + 1, tw, 0);
+}
+template <typename T, int DIR>
+__device__ __forceinline__ void fft_col_pass_dense_in(cx<T> *buf, int N1, int N2, const cx<T> *tw, int lane) {
+    const bool active = lane < N2;
+    switch (N1) {
+#define IBF_CASE(P) case P: fft_col_task_dense_in<T, P, DIR>(buf, lane, active, N2, tw); break;
+        IBF_FFT_SIZES(IBF_CASE)
+#undef IBF_CASE
+        default: break;
+    }
+}
+
 // Batch of nseq sequences at buf + s * sstride.  Ends with a __syncthreads().
 template <typename T, int DIR>
 __device__ __forceinline__ void fft_batch(cx<T> *buf, int nseq, int sstride, int N1, int N2, const FDiv &fN1,

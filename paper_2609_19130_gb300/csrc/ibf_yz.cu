@@ -81,6 +81,14 @@ __device__ __forceinline__ void fft1_warp_fwd(cx<float> *buf, int sstride, int N
     fft_row_pass<float, -1>(buf, 1, sstride, N1, N2, fN1, tw, lane, 32);
     __syncwarp();
 }
+// the same transform of a plane copied dense (row stride N2) into a buffer of the padded size
+__device__ __noinline__ void fft1_warp_fwd_dense(cx<float> *buf, int sstride, int N1, int N2, const FDiv fN1,
+                                                 const cx<float> *tw, int lane) {
+    fft_col_pass_dense_in<float, -1>(buf, N1, N2, tw, lane);
+    __syncwarp();
+    fft_row_pass<float, -1>(buf, 1, sstride, N1, N2, fN1, tw, lane, 32);
+    __syncwarp();
+}
 __device__ __forceinline__ void fft1_warp_inv(cx<float> *buf, int sstride, int N1, int N2, const FDiv &fN1,
                                               const FDiv &fN2, const cx<float> *tw, int lane) {
     fft_row_pass<float, +1>(buf, 1, sstride, N1, N2, fN1, tw, lane, 32);
@@ -228,8 +236,8 @@ __device__ void yzbwd_pipe(const Work &w, const GridDev &G, int cb, unsigned cha
 // The planes of the column block go in rounds of kBulkPlanes: in round r one thread
 // issues bulk asynchronous copies (cp.async.bulk, completed on an mbarrier per buffer)
 // of round r+1's planes into the other of two buffer sets, while
-//   forward:  warps 0..kBulkPlanes-1 each transform one plane of round r (the warp first
-//             moves its dense copy to the padded FFT layout in place), then all threads run
+//   forward:  warps 0..kBulkPlanes-1 each transform one plane of round r (the column
+//             pass reads the dense copy and writes the padded FFT layout in place), then all threads run
 //             the Thomas forward step of the round's planes in order, each thread on fixed
 //             slots, the state d'_{k-1} in registers within the round;
 //   backward: all threads back-substitute the round's planes in order (each thread reads
@@ -241,21 +249,6 @@ __device__ void yzbwd_pipe(const Work &w, const GridDev &G, int cb, unsigned cha
 // the next round overlap the current one.  Waits on the copies give up after
 // kBulkWaitLimit polls and set IBF_ERR_TIMEOUT.
 constexpr int kBulkSlots = 1024 / kYZThreads;  // slots per thread (ny <= 1024)
-
-// In place, by one warp: the dense plane (element p at p) moved to the padded FFT layout
-// (element p at p + p / N2).  Blocks of 32 elements are moved from the last to the first;
-// every target is at or above its source, and the lanes load a block before any stores
-// it, so nothing is overwritten before it is read.
-__device__ __forceinline__ void spread_dense_to_padded(cx<float> *b, int n, int N2, const FDiv &fN2, int lane) {
-    for (int base = ((n - 1) >> 5) << 5; base >= 0; base -= 32) {
-        const int p = base + lane;
-        cx<float> v;
-        if (p < n) v = b[p];
-        __syncwarp();
-        if (p < n) b[pos_nat(p, fN2)] = v;
-        __syncwarp();
-    }
-}
 
 // After a copy of round r was not seen within the wait limit: report IBF_ERR_TIMEOUT and
 // let the copies of round r+1, already issued, land (bounded) before the CTA exits.
@@ -325,7 +318,7 @@ __device__ __noinline__ void yzfwd_bulk_sweep(const Work &w, const GridDev &G, i
 __device__ void yzfwd_bulk(const Work &w, const GridDev &G, int cb, unsigned char *smem) {
     const int ny = G.ny, nz = G.nz, ncb = G.ncb;
     const int N1 = G.ny1, N2 = G.ny2, sstride = fft_seq_len(N1, N2) + 1;
-    const FDiv fN1 = G.fny1, fN2 = G.fny2;
+    const FDiv fN1 = G.fny1;
     const size_t sb = pipe_align16((size_t)max(sstride, ny) * 8);
     auto buf = [&](int set, int f) { return reinterpret_cast<cx<float> *>(smem + (size_t)(set * kBulkPlanes + f) * sb); };
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + 2 * kBulkPlanes * sb);
@@ -360,9 +353,7 @@ __device__ void yzfwd_bulk(const Work &w, const GridDev &G, int cb, unsigned cha
             const int k = r * kBulkPlanes + warp;
             if (k < nz) {
                 if (mbar_wait_bounded(bar + (r & 1) * kBulkPlanes + warp, (unsigned)(r >> 1) & 1u, kBulkWaitLimit)) {
-                    cx<float> *b = buf(r & 1, warp);
-                    spread_dense_to_padded(b, ny, N2, fN2, lane);
-                    fft1_warp_fwd(b, sstride, N1, N2, fN1, fN2, twy, lane);
+                    fft1_warp_fwd_dense(buf(r & 1, warp), sstride, N1, N2, fN1, twy, lane);
                 }
                 else
                     lost = true;
@@ -421,7 +412,6 @@ __device__ void yzbwd_bulk(const Work &w, const GridDev &G, int cb, unsigned cha
     cx<float> st[kBulkSlots];  // phi_hat_{k+1} of this thread's slots
 #pragma unroll
     for (int i = 0; i < kBulkSlots; ++i) st[i] = {0.f, 0.f};
-    bool lost = false;
     for (int r = 0; r < nround; ++r) {
         if (tid == 0 && r + 1 < nround) {
             fence_proxy_async_smem();
@@ -446,21 +436,23 @@ __device__ void yzbwd_bulk(const Work &w, const GridDev &G, int cb, unsigned cha
         for (int f = 0; f < kBulkPlanes; ++f) {
             const int i0 = r * kBulkPlanes + f;
             if (i0 >= nz) break;
-            if (!mbar_wait_bounded(bar + (r & 1) * kBulkPlanes + f, (unsigned)(r >> 1) & 1u, kBulkWaitLimit))
-                lost = true;
-            // a lost copy stops the column block: the error is reported, nothing more is waited on
-            if (__syncthreads_or(lost)) {
-                bulk_lost_cleanup(w, bar, r, nround, nz, tid);
-                return;
-            }
+            // each thread reads its slots of the plane's dense copy once its wait has seen
+            // the copy land; one barrier then both ends the reads (the padded layout of the
+            // same buffer may be written) and tells every thread whether a copy was lost
+            const bool arrived =
+                mbar_wait_bounded(bar + (r & 1) * kBulkPlanes + f, (unsigned)(r >> 1) & 1u, kBulkWaitLimit);
             cx<float> *b = buf(r & 1, f);
             cx<float> dv[kBulkSlots];
 #pragma unroll
             for (int i = 0; i < kBulkSlots; ++i) {
                 const int q = tid + i * kYZThreads;
-                dv[i] = q < ny ? b[q] : cx<float>{0.f, 0.f};
+                dv[i] = (arrived && q < ny) ? b[q] : cx<float>{0.f, 0.f};
             }
-            __syncthreads();  // the plane's dense copy is read: its padded layout may be written
+            // a lost copy stops the column block: the error is reported, nothing more is waited on
+            if (__syncthreads_or(!arrived)) {
+                bulk_lost_cleanup(w, bar, r, nround, nz, tid);
+                return;
+            }
 #pragma unroll
             for (int i = 0; i < kBulkSlots; ++i) {
                 const int q = tid + i * kYZThreads;
