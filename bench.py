@@ -98,14 +98,14 @@ def fp64_peak():
 # kernel from one ncu capture (512x512x128 mixed, two refinement sweeps, see profiles/),
 # valid while the kernel sources hash to NCU_SOURCES_SHA256; otherwise the roofline's
 # traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.46, "x_forward_residual": 15.29, "x_forward_residual2": 19.62,
-                          "correct": 69.95, "yz_forward": 8.42, "yz_backward": 8.39, "x_inverse_store": 6.55,
-                          "x_inverse_accumulate": 6.57, "x_inverse_last": 6.56}
-NCU_SOURCES_SHA256 = "99245cf58dc0f808d550620971c054af74987a69b99c55688c13a2cdb1988224"
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.74, "x_forward_residual": 15.30, "x_forward_residual2": 19.58,
+                          "correct": 69.57, "yz_forward": 8.43, "yz_backward": 8.38, "x_inverse_store": 6.55,
+                          "x_inverse_accumulate": 6.56, "x_inverse_last": 6.56}
+NCU_SOURCES_SHA256 = "cdc45203777bab40d0ae2689737fcbe283df0f21de6696f1e3e968a40583a674"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
                   "ibf_internal.h", "ibf_viscous.h")
 # the same for the viscous solve's kernels (mixed path)
-NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.32}
+NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.31}
 
 
 def kernel_sources_sha256():
@@ -502,6 +502,28 @@ def measure_batch64(args, ws, rank, dev, autotune=True):
     ms = max_over_ranks(e0.elapsed_time(e1) / steps, ws)
     prof = plan.profile_read(reset=True)
     plan.profile(False)
+    # the same step replayed from a CUDA graph (one capture of one ibf_project call): the
+    # difference to the eager time is what issuing the step's launches one by one costs
+    graph = {}
+    try:
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            plan.project_into(ins, outs, DT, 1.0)
+        for _ in range(3):
+            cg.replay()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0.record(st)
+        for _ in range(steps):
+            cg.replay()
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier(ws)
+        gms = max_over_ranks(e0.elapsed_time(e1) / steps, ws)
+        graph = {"ms_per_step": gms, "value": all_cells / (gms * 1e-3), "eager_minus_graph_ms": ms - gms}
+        del cg
+    except Exception as exc:  # capture refused by this torch build: report, keep the eager number
+        graph = {"unavailable": str(exc)[:200]}
     kinds = {}
     for gi in range(len(grids)):
         t = plan.tuning(gi)
@@ -521,8 +543,8 @@ def measure_batch64(args, ws, rank, dev, autotune=True):
                    "l2_policy": f"batch fields {cells * 56 / 1e9:.1f} GB > 129 MB L2: no flush"},
         "kernels": {k: {"launches": c, "ms_per_launch": t / c, "share": t / sum(x[1] for x in prof.values())}
                     for k, (c, t) in prof.items()},
-        "launches_per_step": launches / steps, "gpu_launches": launches,
-        "clocks": ck.summary()}
+        "launches_per_step": launches / steps, "gpu_launches": launches * (2 if "ms_per_step" in graph else 1),
+        "graph_replay": graph, "clocks": ck.summary()}
 
 
 def bench_batch64(args):
