@@ -48,14 +48,19 @@ BYTES_MIXED = {"x_forward_div": 36.0, "yz_forward": 10.0, "yz_backward": 10.0, "
                "x_forward_residual": 16.0, "x_inverse_accumulate": 8.0, "x_forward_residual2": 20.0,
                "x_inverse_accumulate2": 20.0, "x_inverse_last": 8.0, "correct": 64.0, "mode00": 0.0}
 # with two or more sweeps the last correction is kept apart (phi = hi + lo + lo2): the last
-# sweep's inverse x-FFT writes lo2 (4 + 4) and the correction also reads it (64 + 4)
+# sweep's inverse x-FFT writes lo2 (4 + 4) and the correction also reads it (64 + 4); the
+# first sweep's residual is kept per cell (its kernel writes 8 more bytes) and the second
+# sweep reads it instead of b, with delta_1 (4 + neighbours), phi_0 at the cell (4) and
+# writes the spectrum (4): 20
 BYTES_CORRECT_LO2 = 68.0
+BYTES_RESID_KEPT = 24.0
 
 
 def bytes_mixed(refine):
     b = dict(BYTES_MIXED)
     if refine >= 2:
         b["correct"] = BYTES_CORRECT_LO2
+        b["x_forward_residual"] = BYTES_RESID_KEPT
     return b
 BYTES_FP64 = {"x_forward_div": 32.0, "yz_forward": 20.0, "yz_backward": 20.0, "x_inverse_store": 16.0,
               "correct": 56.0, "mode00": 0.0}

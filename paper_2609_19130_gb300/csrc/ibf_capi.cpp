@@ -582,7 +582,10 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         IBF_TRY(dalloc(pl, &w.bdf, sizeof(float2) * (size_t)cells));
         IBF_TRY(dalloc(pl, &w.phi_hi, sizeof(float) * (size_t)cells));
         IBF_TRY(dalloc(pl, &w.phi_lo, sizeof(float) * (size_t)cells));
-        if (pl->opts.refine_steps >= 2) IBF_TRY(dalloc(pl, &w.phi_lo2, sizeof(float) * (size_t)cells));
+        if (pl->opts.refine_steps >= 2) {
+            IBF_TRY(dalloc(pl, &w.phi_lo2, sizeof(float) * (size_t)cells));
+            IBF_TRY(dalloc(pl, &w.rdf, sizeof(float2) * (size_t)cells));
+        }
         // test hook: IBF_FAULT_LOSE_COPY makes the round-based forward y/z kernel drop one
         // plane copy, so that its bounded wait runs out and IBF_ERR_TIMEOUT is reported
         const char *lose = getenv("IBF_FAULT_LOSE_COPY");
@@ -780,7 +783,9 @@ ibf_status run(ibf_plan *pl, const ibf_fields *in, const ibf_fields *out, double
         // phi) are profiled under their own names
         IBF_TRY(for_chunks(c, lo_valid ? "x_forward_residual2" : "x_forward_residual", in, out,
                            [&](const UserPtrs &p, int nb) {
-            return launch_xfwd(mixed, XM_RESID, w, p, use_ws, lo_valid, nb, s, rs, pl->xsmem, st);
+            // the second sweep starts from the first sweep's stored residual
+            return launch_xfwd(mixed, (r == 1 && w.rdf) ? XM_RESID1 : XM_RESID, w, p, use_ws, lo_valid, nb, s, rs,
+                               pl->xsmem, st);
         }));
         IBF_TRY(solve_core(c, 0));
         IBF_TRY(for_chunks(c, last ? "x_inverse_last" : (lo_valid ? "x_inverse_accumulate2" : "x_inverse_accumulate"),

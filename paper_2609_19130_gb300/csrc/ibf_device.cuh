@@ -212,6 +212,23 @@ __device__ __forceinline__ df2 df_sub2(df2 a, df2 b) {
     const float2 e = p2sub(p2sub(a.hi, p2sub(s, bb)), p2add(b.hi, bb));
     return quick_two_sum2(s, p2add(e, p2sub(a.lo, b.lo)));
 }
+// a - b for float-float pairs that need not be normalised (phi = hi + lo during the
+// refinement), to the pairs' precision: the leading words' difference exactly (a two-sum),
+// the trailing words' difference rounded once to a float, and that float added to the
+// exact pair by a second two-sum.  The one rounding that is not at the pair's precision
+// is fl(a.lo - b.lo), which the refinement residual reproduces (k_xfwd, XM_RESID1), so that
+// it cancels in the divergence of the corrected velocity.
+__device__ __forceinline__ df df_sub_acc(df a, df b) {
+    const df s = two_sum(a.hi, -b.hi);
+    const df t = two_sum(s.hi, __fsub_rn(a.lo, b.lo));
+    return quick_two_sum(t.hi, __fadd_rn(t.lo, s.lo));
+}
+__device__ __forceinline__ df2 df_sub2_acc(df2 a, df2 b) {  // lane for lane df_sub_acc
+    const float2 s = p2sub(a.hi, b.hi), bb = p2sub(s, a.hi);
+    const float2 e = p2sub(p2sub(a.hi, p2sub(s, bb)), p2add(b.hi, bb));
+    const df2 t = two_sum2(s, p2sub(a.lo, b.lo));
+    return quick_two_sum2(t.hi, p2add(t.lo, e));
+}
 // df_mul of one float-float c by two values: lane for lane the scalar df_mul(c, d) (the
 // leading product formed negated, which rounds as its negation)
 __device__ __forceinline__ df2 df_mul2(df c, df2 d) {
@@ -363,6 +380,7 @@ struct F64Arith {
     __device__ __forceinline__ static double store_once(V v) { return v; }
     __device__ __forceinline__ static V add(V a, V b) { return a + b; }
     __device__ __forceinline__ static V sub(V a, V b) { return a - b; }
+    __device__ __forceinline__ static V sub_acc(V a, V b) { return a - b; }
     __device__ __forceinline__ static V mul(V a, V b) { return a * b; }
     __device__ __forceinline__ static V from_f(float a) { return (double)a; }
     __device__ __forceinline__ static V zero() { return 0.0; }
@@ -376,6 +394,8 @@ struct DFArith {
     __device__ __forceinline__ static double store_once(V v) { return df_to_f64_general(v); }
     __device__ __forceinline__ static V add(V a, V b) { return df_add(a, b); }
     __device__ __forceinline__ static V sub(V a, V b) { return df_sub(a, b); }
+    // differences of a refined phi (unnormalised pairs): see df_sub_acc
+    __device__ __forceinline__ static V sub_acc(V a, V b) { return df_sub_acc(a, b); }
     __device__ __forceinline__ static V mul(V a, V b) { return df_mul(a, b); }
     __device__ __forceinline__ static V from_f(float a) { return df_make(a); }
     __device__ __forceinline__ static V zero() { return df_make(0.f); }

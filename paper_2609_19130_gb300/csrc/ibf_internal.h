@@ -116,6 +116,8 @@ struct Work {
     double *phi_ws;            // per-cell fp64 phi of the adjoint solve / of a pressure update (fp64 path)
     double *bws;               // per-cell fp64 right-hand side (fp64 path with the implicit pressure update)
     float *phi_hi, *phi_lo;    // per-cell float-float phi being refined (mixed path)
+    float2 *rdf;               // per-cell float-float residual of the first refinement sweep (mixed path
+                               // with two or more sweeps; else null): the second sweep's starts from it
     float *phi_lo2;            // per-cell correction of the last refinement sweep, kept apart so that
                                // phi = hi + lo + lo2 carries more bits than a float-float pair
                                // (mixed path with two or more sweeps; else null)
@@ -143,7 +145,8 @@ struct UserPtrs {
 // x-forward modes: right-hand side of the first solve, refinement residual (phi a
 // float-float pair), adjoint source, refinement residual of the first sweep (phi plain fp32)
 enum XMode { XM_DIV = 0, XM_RESID = 1, XM_ADJ = 2, XM_RESID0 = 3, XM_DIVQ = 4 /* XM_DIV with a mass source q */,
-             XM_COPY = 5 /* the field in_u itself (viscous solve): no stencil, no plane sums */ };
+             XM_COPY = 5 /* the field in_u itself (viscous solve): no stencil, no plane sums */,
+             XM_RESID1 = 6 /* second sweep: the first sweep's residual less L of its correction */ };
 enum InvMode { IM_STORE = 0, IM_ACCUM = 1, IM_LAST = 2 /* the last sweep's correction into phi_lo2 */ };
 
 // Launchers (ibf_kernels.cu).  T = 0: fp64 path, 1: mixed path.

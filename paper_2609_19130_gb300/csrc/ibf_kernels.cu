@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
         const int ii = act ? i : nx - 1;  // inactive lanes load a valid cell and discard it
         // right neighbour: the next face of the u row (face nx when x is wall-bounded) on
         // the divergence paths, the next cell (periodic wrap) on the residual path
-        const int ip = (ii + 1 == nx && (MODE == XM_RESID || MODE == XM_RESID0 || !wall_x)) ? 0 : ii + 1;
+        const int ip = (ii + 1 == nx && (MODE == XM_RESID || MODE == XM_RESID0 || MODE == XM_RESID1 || !wall_x)) ? 0 : ii + 1;
         const int im = (ii == 0) ? nx - 1 : ii - 1;
         const bool own_up = (lane == 31) || (ii + 1 == nx);
         const bool own_dn = (lane == 0) || (ii == 0);
@@ -405,6 +405,11 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                     const df2 r = df_resid4_2(bv2, cp, cu, d2x, cv, d2y, cwp, dzp, cwm, dzm);
                     const float2 val = p2mul(p2add(r.hi, r.lo), make_float2(scale, scale));
                     const bool u0 = act && live[0], u1 = act && live[1];
+                    if (w.rdf) {  // two or more sweeps: the second starts from this residual
+                        float2 *rd = w.rdf + G.cell_off + pbase + (j0 + jl0) * nx + i;
+                        if (u0) rd[0] = make_float2(r.hi.x, r.lo.x);
+                        if (u1) rd[nx] = make_float2(r.hi.y, r.lo.y);
+                    }
 #pragma unroll
                     for (int f = 0; f < NF; ++f)
                         acc2 = df_addf2(acc2, make_float2(u0 ? pc[f][0] : 0.f, u1 ? pc[f][1] : 0.f));
@@ -425,12 +430,126 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
             }
             acc_phi = df_add(acc_phi, df_add(df{acc2.hi.x, acc2.lo.x}, df{acc2.hi.y, acc2.lo.y}));
             acc = df_add(acc, df_add(df{accr.hi.x, accr.lo.x}, df{accr.hi.y, accr.lo.y}));
+        } else if constexpr (MODE == XM_RESID1 && IsDF<A>::value) {
+            // second refinement sweep: phi = phi_0 + delta_1 (hi, lo), and the first sweep's
+            // residual r_1 = b - <b> - L phi_0 is kept per cell, so r_2 = r_1 - L delta_1.
+            // delta_1's first differences are rounded to fp32 exactly as the velocity
+            // correction rounds the trailing words' differences (df_sub_acc), so that this
+            // rounding cancels in D u; the second differences of those floats are exact
+            // float-float pairs, then products and sums as in the first sweep, two rows at
+            // a time.  phi_0 is read at the cell only, for the plane sums of phi.
+            const float *dl = w.phi_lo + G.cell_off + pbase, *p0 = w.phi_hi + G.cell_off + pbase;
+            const float2 *rd = w.rdf + G.cell_off + pbase;
+            constexpr int RG = kRowGroup;
+            float Dm = 0.f, Dc = 0.f;
+            bool have = false;
+            df2 acc2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of phi, per lane
+            df2 accr = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // plane sum of the residual, per lane
+            for (int jg = sm.r0; jg < sm.r1; jg += RG) {
+                float pn[RG], pkp[RG], pkm[RG], peu[RG], ped[RG], ph0[RG];
+                float2 rv[RG];
+                float pm0 = 0.f, pc0 = 0.f;
+                const bool need0 = !have;
+#pragma unroll
+                for (int q = 0; q < RG; ++q) {
+                    const int jl = jg + q, j = j0 + jl;
+                    pn[q] = pkp[q] = pkm[q] = peu[q] = ped[q] = ph0[q] = 0.f;
+                    rv[q] = make_float2(0.f, 0.f);
+                    if (jl < sm.r1 && j < ny) {
+                        const int jp = (j + 1 == ny) ? 0 : j + 1;
+                        const int jm = (j == 0) ? ny - 1 : j - 1;
+                        const int row = j * nx;
+                        if (q == 0 && need0) {
+                            pm0 = __ldg(dl + jm * nx + ii);
+                            pc0 = __ldg(dl + row + ii);
+                        }
+                        pn[q] = __ldg(dl + jp * nx + ii);
+                        if (k + 1 < nz) pkp[q] = __ldg(dl + plane + row + ii);
+                        if (k > 0) pkm[q] = __ldg(dl + row + ii - plane);
+                        if (own_up) peu[q] = __ldg(dl + row + ip);
+                        if (own_dn) ped[q] = __ldg(dl + row + im);
+                        if (act) {
+                            rv[q] = __ldg(rd + row + i);
+                            ph0[q] = __ldg(p0 + row + i);
+                        }
+                    }
+                }
+                if (need0) {
+                    Dm = pm0;
+                    Dc = pc0;
+                }
+#pragma unroll
+                for (int q = 0; q < RG; q += 2) {
+                    const int jl0 = jg + q;
+                    if (jl0 >= sm.r1) break;  // warp-uniform
+                    float xp[2], xm[2], yp[2], ym[2], zp[2], zm[2], pc[2];
+                    bool live[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = j0 + jl0 + h;
+                        live[h] = jl0 + h < sm.r1 && j < ny;
+                        const float P = Dc;
+                        float Pip = __shfl_down_sync(0xffffffffu, P, 1);
+                        if (own_up) Pip = peu[q + h];
+                        float Pim = __shfl_up_sync(0xffffffffu, P, 1);
+                        if (own_dn) Pim = ped[q + h];
+                        // wall faces carry no gradient: the neighbour is the cell itself
+                        if (wall_x && ii + 1 == nx) Pip = P;
+                        if (wall_x && ii == 0) Pim = P;
+                        float Pjp = pn[q + h], Pjm = Dm;
+                        if (wall_y && j + 1 == ny) Pjp = P;
+                        if (wall_y && j == 0) Pjm = P;
+                        xp[h] = Pip; xm[h] = Pim; yp[h] = Pjp; ym[h] = Pjm; pc[h] = P;
+                        // top: Neumann (difference zero) or Dirichlet outlet (phi = 0 on the face)
+                        zp[h] = (k + 1 < nz) ? pkp[q + h] : (G.dir_top ? 0.f : P);
+                        zm[h] = (k > 0) ? pkm[q + h] : P;
+                        if (live[h]) {
+                            Dm = P;
+                            Dc = pn[q + h];
+                        }
+                        have = live[h];
+                    }
+                    const float2 PC = make_float2(pc[0], pc[1]);
+                    // first differences rounded to fp32 (the correction's fl(lo_a - lo_b)),
+                    // second differences exact
+                    const float2 fxp = p2sub(make_float2(xp[0], xp[1]), PC), fxm = p2sub(PC, make_float2(xm[0], xm[1]));
+                    const float2 fyp = p2sub(make_float2(yp[0], yp[1]), PC), fym = p2sub(PC, make_float2(ym[0], ym[1]));
+                    const df2 d2x = two_sum2(fxp, p2mul(fxm, make_float2(-1.f, -1.f)));
+                    const df2 d2y = two_sum2(fyp, p2mul(fym, make_float2(-1.f, -1.f)));
+                    const df2 dzp = {p2sub(make_float2(zp[0], zp[1]), PC), make_float2(0.f, 0.f)};
+                    const df2 dzm = {p2sub(PC, make_float2(zm[0], zm[1])), make_float2(0.f, 0.f)};
+                    const df2 r1 = {make_float2(rv[q].x, rv[q + 1].x), make_float2(rv[q].y, rv[q + 1].y)};
+                    const df zero = {0.f, 0.f};
+                    const df2 r = df_resid4_2(r1, zero, cu, d2x, cv, d2y, cwp, dzp, cwm, dzm);
+                    const float2 val = p2mul(p2add(r.hi, r.lo), make_float2(scale, scale));
+                    const bool u0 = act && live[0], u1 = act && live[1];
+                    acc2 = df_addf2(acc2, make_float2(u0 ? ph0[q] : 0.f, u1 ? ph0[q + 1] : 0.f));
+                    acc2 = df_addf2(acc2, make_float2(u0 ? pc[0] : 0.f, u1 ? pc[1] : 0.f));
+                    accr = df_add2(accr, df2{make_float2(u0 ? r.hi.x : 0.f, u1 ? r.hi.y : 0.f),
+                                             make_float2(u0 ? r.lo.x : 0.f, u1 ? r.lo.y : 0.f)});
+                    if (act) {
+                        const float v0 = u0 ? val.x : 0.f, v1 = u1 ? val.y : 0.f;
+                        float *slot = reinterpret_cast<float *>(buf + (jl0 >> 1) * sstride + spos);
+                        if ((jl0 & 1) == 0 && jl0 + 1 < sm.r1) {
+                            *reinterpret_cast<float2 *>(slot) = make_float2(v0, v1);
+                        } else {
+                            slot[jl0 & 1] = v0;
+                            if (jl0 + 1 < sm.r1)
+                                *(reinterpret_cast<float *>(buf + ((jl0 + 1) >> 1) * sstride + spos) + ((jl0 + 1) & 1)) = v1;
+                        }
+                    }
+                }
+            }
+            acc_phi = df_add(acc_phi, df_add(df{acc2.hi.x, acc2.lo.x}, df{acc2.hi.y, acc2.lo.y}));
+            acc = df_add(acc, df_add(df{accr.hi.x, accr.lo.x}, df{accr.hi.y, accr.lo.y}));
         } else if constexpr (MODE == XM_RESID && IsDF<A>::value) {
-            // a later refinement sweep: phi = hi + lo (float-float, possibly unnormalised).
-            // The first differences of phi are formed exactly as the velocity correction
-            // forms them (df_sub, lane for lane), so that their rounding is part of the
-            // residual this sweep corrects and cancels in D u; second differences, products
-            // and sums as in the first sweep, two rows at a time in packed operations.
+            // a later refinement sweep (the third and after; the second is XM_RESID1 where
+            // the first sweep's residual is kept): phi = hi + lo (float-float, possibly
+            // unnormalised).  The first differences of phi are formed exactly as the velocity
+            // correction forms them (df_sub_acc, lane for lane), so that their one fp32
+            // rounding is part of the residual this sweep corrects and cancels in D u; second
+            // differences, products and sums as in the first sweep, two rows at a time in
+            // packed operations.
             const float *phw[2] = {w.phi_hi + G.cell_off + pbase, w.phi_lo + G.cell_off + pbase};
             const float2 *bd = w.bdf + G.cell_off + pbase;
             float Pm[2] = {0.f, 0.f}, Pc[2] = {0.f, 0.f};
@@ -514,10 +633,10 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
                     return df2{make_float2(a[0][0], a[0][1]), make_float2(a[1][0], a[1][1])};
                 };
                 const df2 PC = pair(pc);
-                const df2 d2x = df_sub2(df_sub2(pair(xp), PC), df_sub2(PC, pair(xm)));
-                const df2 d2y = df_sub2(df_sub2(pair(yp), PC), df_sub2(PC, pair(ym)));
-                const df2 dzp = df_sub2(pair(zp), PC);
-                const df2 dzm = df_sub2(PC, pair(zm));
+                const df2 d2x = df_sub2(df_sub2_acc(pair(xp), PC), df_sub2_acc(PC, pair(xm)));
+                const df2 d2y = df_sub2(df_sub2_acc(pair(yp), PC), df_sub2_acc(PC, pair(ym)));
+                const df2 dzp = df_sub2_acc(pair(zp), PC);
+                const df2 dzm = df_sub2_acc(PC, pair(zm));
                 const df2 bv2 = {make_float2(bdv[0].x, bdv[1].x), make_float2(bdv[0].y, bdv[1].y)};
                 const df2 r = df_resid4_2(bv2, cp, cu, d2x, cv, d2y, cwp, dzp, cwm, dzm);
                 const float2 val = p2mul(p2add(r.hi, r.lo), make_float2(scale, scale));
@@ -627,7 +746,7 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
         V tot = Red<A>::sum(acc, red);
         if (threadIdx.x == 0) w.partial[pslot] = A::store_once(tot);
     }
-    if (MODE == XM_RESID || MODE == XM_RESID0) {
+    if (MODE == XM_RESID || MODE == XM_RESID0 || MODE == XM_RESID1) {
         V totp = Red<A>::sum(acc_phi, red);
         if (threadIdx.x == 0) w.partial_phi[pslot] = A::store_once(totp);
     }
@@ -1008,9 +1127,9 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? (L2 ? 4 : 5) : 3)
                         }
                         return t;
                     };
-                    const df2 tx = term2(cu, df_sub2(pk(Pims), P), pkf(dlx));
-                    const df2 ty = term2(cv, df_sub2(pk(Pjws), P), pkf(dly));
-                    const df2 tz = term2(cw, df_sub2(ZM, P), pkf(dlz));
+                    const df2 tx = term2(cu, df_sub2_acc(pk(Pims), P), pkf(dlx));
+                    const df2 ty = term2(cv, df_sub2_acc(pk(Pjws), P), pkf(dly));
+                    const df2 tz = term2(cw, df_sub2_acc(ZM, P), pkf(dlz));
                     df2 tt = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
                     if (k == nz - 1 && G.dir_top) tt = term2(cwt, P, pkf(Lcs));
                     df2 Pn = P;
@@ -1078,14 +1197,14 @@ __global__ void __launch_bounds__(kXThreads, IsDF<A>::value ? (L2 ? 4 : 5) : 3)
                     // the correction t is formed in the solve's high precision; the face
                     // value u* + t is one fp64 add (the fp64 pipe is otherwise idle here)
                     const int c = row + i;
-                    uo[j * nxu + i] = ru[q] + term(cu, A::sub(Pim, Pc), dlx);
-                    vo[c] = rv[q] + term(cv, A::sub(Pjw, Pc), dly);
+                    uo[j * nxu + i] = ru[q] + term(cu, A::sub_acc(Pim, Pc), dlx);
+                    vo[c] = rv[q] + term(cv, A::sub_acc(Pjw, Pc), dly);
                     if (ADJ) {
-                        wo[c] = rw[q] + term(A::from_f(1.f), A::sub(pkm[q], Pc), dlz);
+                        wo[c] = rw[q] + term(A::from_f(1.f), A::sub_acc(pkm[q], Pc), dlz);
                         if (k == nz - 1) wo[c + plane] = rwt[q] + phi_out(Pc);
                     } else {
                         if (k == 0) wo[c] = rw[q];
-                        else wo[c] = rw[q] + term(cw, A::sub(pkm[q], Pc), dlz);
+                        else wo[c] = rw[q] + term(cw, A::sub_acc(pkm[q], Pc), dlz);
                         if (k == nz - 1)  // outlet face: corrected with a Dirichlet outlet, else a wall
                             wo[c + plane] = G.dir_top ? rwt[q] + term(cwt, Pc, Lc) : rwt[q];
                         if (po) {
@@ -1200,7 +1319,10 @@ cudaError_t launch_xfwd_mixed(int mode, const Work &w, const UserPtrs &p, int us
         k_xfwd<float, DFArith, XM_RESID0, W, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
     else if (mode == XM_RESID)
         k_xfwd<float, DFArith, XM_RESID, W, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
-    else if (mode == XM_COPY) {
+    else if (mode == XM_RESID1) {
+        if (!w.rdf) return cudaErrorInvalidValue;  // the first sweep's residual is not kept
+        k_xfwd<float, DFArith, XM_RESID1, W, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
+    } else if (mode == XM_COPY) {
         if constexpr (W) return cudaErrorInvalidValue;  // periodic x and y only
         else k_xfwd<float, DFArith, XM_COPY, false, SPLIT><<<gr, nt, smem, st>>>(w, p, use_ws, lo_valid, s, rs);
     } else
@@ -1337,11 +1459,13 @@ cudaError_t set_smem_limits(int mixed) {
             set((const void *)k_xfwd<float, DFArith, XM_DIVQ, W, 1>);
             set((const void *)k_xfwd<float, DFArith, XM_RESID, W, 1>);
             set((const void *)k_xfwd<float, DFArith, XM_RESID0, W, 1>);
+            set((const void *)k_xfwd<float, DFArith, XM_RESID1, W, 1>);
             set((const void *)k_xfwd<float, DFArith, XM_ADJ, W, 1>);
             set((const void *)k_xfwd<float, DFArith, XM_DIV, W, 2>);
             set((const void *)k_xfwd<float, DFArith, XM_DIVQ, W, 2>);
             set((const void *)k_xfwd<float, DFArith, XM_RESID, W, 2>);
             set((const void *)k_xfwd<float, DFArith, XM_RESID0, W, 2>);
+            set((const void *)k_xfwd<float, DFArith, XM_RESID1, W, 2>);
             set((const void *)k_xfwd<float, DFArith, XM_ADJ, W, 2>);
             set((const void *)k_xinv<float, DFArith, IM_STORE, W, 1>);
             set((const void *)k_xinv<float, DFArith, IM_ACCUM, W, 1>);
