@@ -38,9 +38,12 @@ constexpr int kRowGroup = 4;  // rows whose loads are issued together (memory-le
 // W: the launch contains wall-bounded grids (compiled out of periodic-only plans).
 // SPLIT = 2 (mixed path, rows divisible by 4): two CTAs of kXThreads / 2 threads per
 // row block, each forming and transforming half of its rows, so that one CTA's
-// transform overlaps another's loads; each half writes its own plane-sum slot.
+// transform overlaps another's loads; each half writes its own plane-sum slot.  Five
+// half-block CTAs per SM (96 registers: 20 warps to hide latency) except for the later
+// sweeps' residuals, whose stencils need the 128 registers of four.
 template <typename T, class A, int MODE, bool W, int SPLIT>
-__global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? ((MODE == XM_RESID || MODE == XM_RESID1) ? 4 : 5)
+                                                               : (sizeof(T) == 4 ? 2 : 1))
     k_xfwd(Work w, UserPtrs p, int use_ws, int lo_valid, double s, double rs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
@@ -811,9 +814,10 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T)
 // refinement correction to the float-float phi.
 // SPLIT = 2: two CTAs of kXThreads / 2 threads per row block, each transforming half
 // of its rows (every grid of the plan has rows divisible by 4): twice the CTAs per SM
-// at the same warp count, so that one CTA's FFT overlaps another's gather and store.
+// at the same warp count, so that one CTA's FFT overlaps another's gather and store;
+// five of them per SM (96 registers).
 template <typename T, class A, int IMODE, bool W, int SPLIT>
-__global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 4 : (sizeof(T) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 5 : (sizeof(T) == 4 ? 2 : 1))
     k_xinv(Work w, UserPtrs p, int use_ws, int lo_valid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
