@@ -103,14 +103,14 @@ def fp64_peak():
 # kernel from one ncu capture (512x512x128 mixed, two refinement sweeps, see profiles/),
 # valid while the kernel sources hash to NCU_SOURCES_SHA256; otherwise the roofline's
 # traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.74, "x_forward_residual": 15.30, "x_forward_residual2": 19.58,
-                          "correct": 69.57, "yz_forward": 8.43, "yz_backward": 8.38, "x_inverse_store": 6.55,
-                          "x_inverse_accumulate": 6.56, "x_inverse_last": 6.56}
-NCU_SOURCES_SHA256 = "cdc45203777bab40d0ae2689737fcbe283df0f21de6696f1e3e968a40583a674"
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.53, "x_forward_residual": 22.93, "x_forward_residual2": 19.42,
+                          "correct": 69.62, "yz_forward": 8.42, "yz_backward": 8.41, "x_inverse_store": 6.50,
+                          "x_inverse_accumulate": 6.51, "x_inverse_last": 6.51}
+NCU_SOURCES_SHA256 = "a3ef44868b0fb0921b92c0eb49a27c915953197b83ecdc54800c7df22dfdd8ec"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
                   "ibf_internal.h", "ibf_viscous.h")
 # the same for the viscous solve's kernels (mixed path)
-NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.31}
+NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.32}
 
 
 def kernel_sources_sha256():
