@@ -324,6 +324,8 @@ __device__ void yzfwd_bulk(const Work &w, const GridDev &G, int cb, unsigned cha
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + 2 * kBulkPlanes * sb);
     const cx<float> *spec = reinterpret_cast<const cx<float> *>(w.spec) + G.spec_off;
     const cx<float> *twy = reinterpret_cast<const cx<float> *>(w.twy) + G.twy_off;
+    const float *tab = reinterpret_cast<const float *>(w.tab) + G.tab_off;
+    const bool tab_pf = ((G.tab_off | ny) & 3) == 0;  // pivot rows 16-byte aligned
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nround = (nz + kBulkPlanes - 1) / kBulkPlanes;
     const unsigned bytes = (unsigned)ny * 8u;
@@ -340,6 +342,8 @@ __device__ void yzfwd_bulk(const Work &w, const GridDev &G, int cb, unsigned cha
             unsigned long long *b = bar + (r & 1) * kBulkPlanes + f;
             mbar_arrive_expect_tx(b, bytes);
             bulk_g2s(buf(r & 1, f), spec + ((size_t)k * ncb + cb) * ny, bytes, b);
+            // the plane's pivots, read by the sweep of round r: into L2 meanwhile
+            if (tab_pf) bulk_prefetch_l2(tab + ((size_t)k * ncb + cb) * ny, (unsigned)ny * 4u);
         }
     };
     if (tid == 0) issue(0);
@@ -388,6 +392,7 @@ __device__ void yzbwd_bulk(const Work &w, const GridDev &G, int cb, unsigned cha
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + 2 * kBulkPlanes * sb);
     cx<float> *spec = reinterpret_cast<cx<float> *>(w.spec) + G.spec_off;
     const float *tab = reinterpret_cast<const float *>(w.tab) + G.tab_off;
+    const bool tab_pf = ((G.tab_off | ny) & 3) == 0;  // pivot rows 16-byte aligned
     const cx<float> *twy = reinterpret_cast<const cx<float> *>(w.twy) + G.twy_off;
     const float *cz = w.z.czf + G.z_off;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -406,6 +411,8 @@ __device__ void yzbwd_bulk(const Work &w, const GridDev &G, int cb, unsigned cha
             unsigned long long *b = bar + (r & 1) * kBulkPlanes + f;
             mbar_arrive_expect_tx(b, bytes);
             bulk_g2s(buf(r & 1, f), spec + ((size_t)k * ncb + cb) * ny, bytes, b);
+            // the plane's pivots, read at the start of round r: into L2 meanwhile
+            if (tab_pf) bulk_prefetch_l2(tab + ((size_t)k * ncb + cb) * ny, (unsigned)ny * 4u);
         }
     };
     if (tid == 0) issue(0);
