@@ -584,7 +584,10 @@ ibf_status build_plan(ibf_plan *pl, const ibf_grid *grids, int ngrids, const ibf
         IBF_TRY(dalloc(pl, &w.phi_lo, sizeof(float) * (size_t)cells));
         if (pl->opts.refine_steps >= 2) {
             IBF_TRY(dalloc(pl, &w.phi_lo2, sizeof(float) * (size_t)cells));
-            IBF_TRY(dalloc(pl, &w.rdf, sizeof(float2) * (size_t)cells));
+            // test hook: IBF_NO_KEPT_RESIDUAL makes the second sweep form its residual from
+            // phi (b - <b> - L(phi_0 + delta_1)) instead of from the kept first residual
+            const char *nokeep = getenv("IBF_NO_KEPT_RESIDUAL");
+            if (!(nokeep && atoi(nokeep) > 0)) IBF_TRY(dalloc(pl, &w.rdf, sizeof(float2) * (size_t)cells));
         }
         // test hook: IBF_FAULT_LOSE_COPY makes the round-based forward y/z kernel drop one
         // plane copy, so that its bounded wait runs out and IBF_ERR_TIMEOUT is reported
