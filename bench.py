@@ -103,10 +103,10 @@ def fp64_peak():
 # kernel from one ncu capture (512x512x128 mixed, two refinement sweeps, see profiles/),
 # valid while the kernel sources hash to NCU_SOURCES_SHA256; otherwise the roofline's
 # traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.53, "x_forward_residual": 22.93, "x_forward_residual2": 19.42,
-                          "correct": 69.62, "yz_forward": 8.42, "yz_backward": 8.41, "x_inverse_store": 6.50,
-                          "x_inverse_accumulate": 6.51, "x_inverse_last": 6.51}
-NCU_SOURCES_SHA256 = "a3ef44868b0fb0921b92c0eb49a27c915953197b83ecdc54800c7df22dfdd8ec"
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.54, "x_forward_residual": 22.94, "x_forward_residual2": 19.42,
+                          "correct": 69.62, "yz_forward": 8.44, "yz_backward": 8.42, "x_inverse_store": 6.50,
+                          "x_inverse_accumulate": 6.52, "x_inverse_last": 6.53}
+NCU_SOURCES_SHA256 = "b3bc92311945c423fc55ca37a5884a11a1bceb0afc5038284715c07777a6e3e7"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
                   "ibf_internal.h", "ibf_viscous.h")
 # the same for the viscous solve's kernels (mixed path)
