@@ -264,7 +264,8 @@ __device__ __forceinline__ void bulk_lost_cleanup(const Work &w, unsigned long l
 // The Thomas forward step of one round's planes (yzfwd_bulk), in a function of its own so
 // that its pointers and the round's loads are not live across the transforms, which need
 // the whole 128-register budget.
-__device__ __noinline__ void yzfwd_bulk_sweep(const Work &w, const GridDev &G, int cb, unsigned char *smem, int r) {
+__device__ __noinline__ bool yzfwd_bulk_sweep(const Work &w, const GridDev &G, int cb, unsigned char *smem, int r,
+                                             bool lost) {
     const int ny = G.ny, nz = G.nz, ncb = G.ncb;
     const int sstride = fft_seq_len(G.ny1, G.ny2) + 1;
     const FDiv fN2 = G.fny2;
@@ -293,6 +294,9 @@ __device__ __noinline__ void yzfwd_bulk_sweep(const Work &w, const GridDev &G, i
             inv[f][i] = q < ny ? __ldg(t + q) : 0.f;
         }
     }
+    // the round's transforms are done (and every thread's loads above are in flight)
+    // once all threads pass this barrier; a lost copy stops the column block
+    if (__syncthreads_or(lost)) return true;
 #pragma unroll
     for (int f = 0; f < kBulkPlanes; ++f) {
         const int k = r * kBulkPlanes + f;
@@ -313,6 +317,7 @@ __device__ __noinline__ void yzfwd_bulk_sweep(const Work &w, const GridDev &G, i
             }
         }
     }
+    return false;
 }
 
 __device__ void yzfwd_bulk(const Work &w, const GridDev &G, int cb, unsigned char *smem) {
@@ -363,14 +368,14 @@ __device__ void yzfwd_bulk(const Work &w, const GridDev &G, int cb, unsigned cha
                     lost = true;
             }
         }
-        // a lost copy stops the column block: the error is reported, nothing more is waited on
-        if (__syncthreads_or(lost)) {
+        // the sweep reads back, as the Thomas state, what each thread stored for the last
+        // plane of the previous round (rather than holding it across the transforms); its
+        // loads are issued before the barrier that ends the transforms.  A lost copy stops
+        // the column block: the error is reported, nothing more is waited on
+        if (yzfwd_bulk_sweep(w, G, cb, smem, r, lost)) {
             bulk_lost_cleanup(w, bar, r, nround, nz, tid);
             return;
         }
-        // the sweep reads back, as the Thomas state, what each thread stored for the last
-        // plane of the previous round (rather than holding it across the transforms)
-        yzfwd_bulk_sweep(w, G, cb, smem, r);
         fence_proxy_async_smem();  // this thread's reads of the set before its next copies
         __syncthreads();
     }
