@@ -840,7 +840,43 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? 5 : (sizeof(T)
     const cx<T> *twx = reinterpret_cast<const cx<T> *>(w.twx) + G.twx_off;
     const int npair = rows >> 1;
     const int nload = ncb * npair * mb;
-    if (!(W && G.wall_x)) {
+    if (sizeof(T) == 4 && !(W && G.wall_x) && mb == 1 && ((G.spec_off | ny | j0) & 1) == 0) {
+        // one x-mode per column block (the spectrum of mode m is a run of ny values): the
+        // row pair's two values A_m, B_m are adjacent, so one 16-byte load brings both and
+        // the packed FFT input is formed on the spot, Z_m = A_m + i B_m and
+        // Z_{nx-m} = conj(A_m) + i conj(B_m), with no staging pass
+        // (kGatherBatch loads in flight per thread before any of them is used)
+        constexpr int kGatherBatch = 8;
+        const int nt = npair * nxh, nthr = blockDim.x;
+        for (int t0 = threadIdx.x; t0 < nt; t0 += kGatherBatch * nthr) {
+            float4 v[kGatherBatch];
+            int mq[kGatherBatch], sq[kGatherBatch];
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u) {
+                const int t = t0 + u * nthr;
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                mq[u] = -1;
+                sq[u] = 0;
+                if (t < nt) {
+                    const int m = (int)fdiv((unsigned)t, fnpair);
+                    const int s_ = t - m * npair;
+                    const int ja = j0 + 2 * s_;  // even, and ny is even: row ja + 1 exists with row ja
+                    mq[u] = m;
+                    sq[u] = s_;
+                    if (ja < ny) v[u] = __ldg(reinterpret_cast<const float4 *>(spec + (size_t)m * ny + ja));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u) {
+                const int m = mq[u];
+                if (m < 0) continue;
+                cx<T> *seq = buf + sq[u] * sstride;
+                seq[pos_tr(m, N1, N2, fN1)] = {(T)(v[u].x - v[u].w), (T)(v[u].y + v[u].z)};
+                if (m != 0 && 2 * m != nx)
+                    seq[pos_tr(nx - m, N1, N2, fN1)] = {(T)(v[u].x + v[u].w), (T)(v[u].z - v[u].y)};
+            }
+        }
+    } else if (!(W && G.wall_x)) {
         // real FFT input Z = X_a + i X_b of the row pair (a, b): Z_m = A_m + i B_m and
         // Z_{nx-m} = conj(A_m) + i conj(B_m).  Every spectrum value is first copied
         // asynchronously straight to shared memory (the whole block's input in flight at
