@@ -767,6 +767,28 @@ __global__ void __launch_bounds__(kXThreads / SPLIT, SPLIT == 2 ? ((MODE == XM_R
     cx<T> *spec = reinterpret_cast<cx<T> *>(w.spec) + G.spec_off + (size_t)k * ncb * ny * mb;
     const int nout = ncb * rows * mb;
     const FDiv fmb = G.fmb, frows = SPLIT == 2 ? G.fnpair : G.frows;  // fnpair: rows / 2
+    if (sizeof(T) == 4 && mb == 1 && !wall_x && ((G.spec_off | ny | j0) & 1) == 0 &&
+        (kXThreads / SPLIT) % (rows >> 1) == 0) {
+        // one x-mode per column block: every thread keeps one row pair (one packed
+        // sequence, rows 2s and 2s + 1, adjacent in the spectrum of a mode) and steps through
+        // the modes; the pair's two values come from the same Z_m and Z_{nx-m} and leave as
+        // one 16-byte store
+        const int npair = rows >> 1;
+        const FDiv fnp = SPLIT == 2 ? G.fnpair2 : G.fnpair;
+        const int m0 = (int)fdiv((unsigned)threadIdx.x, fnp), mstep = (kXThreads / SPLIT) / npair;
+        const int s_ = threadIdx.x - m0 * npair, ja = j0 + 2 * s_;
+        if (ja < ny) {  // ny even: row ja + 1 exists with row ja
+            const cx<T> *seq = buf + s_ * sstride;
+            float4 *dst = reinterpret_cast<float4 *>(spec + ja);
+            for (int m = m0; m < nxh; m += mstep) {
+                const cx<T> Zm = seq[pos_tr(m, N1, N2, fN1)];
+                const cx<T> Zc = seq[pos_tr(m == 0 ? 0 : nx - m, N1, N2, fN1)];
+                dst[(size_t)m * (ny >> 1)] = make_float4((Zm.x + Zc.x) * 0.5f, (Zm.y - Zc.y) * 0.5f,
+                                                         (Zm.y + Zc.y) * 0.5f, (Zc.x - Zm.x) * 0.5f);
+            }
+        }
+        return;
+    }
     if (mb == 1 && (kXThreads / SPLIT) % rows == 0 && !wall_x) {
         // one x-mode per column block: every thread keeps one row jl and steps through
         // the modes m0, m0 + blockDim / rows, ... (the rows of one mode are contiguous
