@@ -103,14 +103,14 @@ def fp64_peak():
 # kernel from one ncu capture (512x512x128 mixed, two refinement sweeps, see profiles/),
 # valid while the kernel sources hash to NCU_SOURCES_SHA256; otherwise the roofline's
 # traffic is null.
-NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.54, "x_forward_residual": 22.94, "x_forward_residual2": 19.42,
-                          "correct": 69.62, "yz_forward": 8.44, "yz_backward": 8.42, "x_inverse_store": 6.50,
-                          "x_inverse_accumulate": 6.52, "x_inverse_last": 6.53}
-NCU_SOURCES_SHA256 = "b3bc92311945c423fc55ca37a5884a11a1bceb0afc5038284715c07777a6e3e7"
+NCU_TRAFFIC_B_PER_CELL = {"x_forward_div": 35.57, "x_forward_residual": 22.95, "x_forward_residual2": 19.41,
+                          "correct": 69.61, "yz_forward": 8.43, "yz_backward": 8.43, "x_inverse_store": 6.49,
+                          "x_inverse_accumulate": 6.51, "x_inverse_last": 6.51}
+NCU_SOURCES_SHA256 = "bddd4ec4a7446bfbed8731152b2e999e3e19d7c2400c4567ff40496e7a98425f"
 KERNEL_SOURCES = ("ibf_kernels.cu", "ibf_yz.cu", "ibf_viscous.cu", "ibf_common.cuh", "ibf_device.cuh",
                   "ibf_internal.h", "ibf_viscous.h")
 # the same for the viscous solve's kernels (mixed path)
-NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.32}
+NCU_VISC_TRAFFIC_B_PER_CELL = {"viscous_y": 6.22, "viscous_z": 17.31}
 
 
 def kernel_sources_sha256():
